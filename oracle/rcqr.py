@@ -1,0 +1,137 @@
+"""The randomized Cholesky QR algorithms in FP64, step by step (oracle; test infrastructure only).
+
+Each driver follows the paper's algorithm in its own order and notation:
+
+* rcholqr    -- Alg. 2 (RCholeskyQR):  P = Theta X;  [S, R] = QR(P);  Q = X R^{-1}.
+* rcholqr2   -- Alg. 3 (RCholeskyQR2): Alg. 2, then A = Q^T Q;  R' = chol(A);
+                R <- R' R;  Q <- Q R'^{-1}.
+* reduced    -- Alg. 5 (reduced RCholeskyQR): P = Theta X, Y = L X;
+                [S, R] = QR(P);  Z = Y R^{-1}.
+* rrrcholqr  -- Alg. 7 (RRRCholQR) with the column normalisation of Sec. 4:
+                D = diag(||X_j||), P = Theta X D^{-1}; [S, R, Pi] = RRQR(P);
+                r = min r with ||R22||_F <= tau ||R||_2;
+                Q = (X Pi_{:,1:r} D_sel^{-1}) R_{1:r,1:r}^{-1};  R <- R_{1:r,:} Pi^T D Pi.
+* rrrcholqr2 -- Alg. 7 followed by one CholeskyQR pass as in Alg. 3 (Sec. 4).
+
+The sketch is the product of the integer levels G (theta.theta_levels) with
+X in FP64 (numpy matmul as the library step), scaled afterwards by
+c = theta_scale(k); for long X it is formed in row blocks whose FP64 partial
+sums are added in order.
+"""
+import numpy as np
+
+from . import linalg
+from .theta import theta_levels, theta_scale
+
+SKETCH_ROW_BLOCK = 1 << 14
+
+
+def sketch(X, k, seed, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK):
+    """P = Theta X (k x n, FP64), Theta rows for global X rows row_offset .. row_offset+m-1 (Alg. 2 step 1)."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    acc = np.zeros((k, n))
+    for r0 in range(0, m, row_block):
+        r1 = min(m, r0 + row_block)
+        G = theta_levels(seed, k, row_offset + r0, r1 - r0, stream)
+        acc += G @ X[r0:r1]
+    return theta_scale(k) * acc
+
+
+def column_norms(X):
+    """D_j = ||X_(:,j)||_2 (Sec. 4, the normalisation matrix)."""
+    X = np.asarray(X, dtype=np.float64)
+    return np.sqrt(np.sum(X * X, axis=0))
+
+
+def rcholqr_from_sketch(X, P):
+    """Alg. 2 steps 2-3 for a given sketch P: returns (Q, S, R)."""
+    S, R = linalg.householder_qr(P)
+    Q = linalg.forward_substitution(X, R)
+    return Q, S, R
+
+
+def rcholqr(X, k, seed):
+    """Alg. 2: returns (Q, S, R)."""
+    P = sketch(X, k, seed)
+    return rcholqr_from_sketch(X, P)
+
+
+def cholqr_pass(Q, R):
+    """Alg. 3 steps 2-4 applied to (Q, R): returns (Q <- Q R'^{-1}, R <- R' R, R')."""
+    A = Q.T @ Q
+    Rp = linalg.cholesky(A)
+    return linalg.forward_substitution(Q, Rp), Rp @ R, Rp
+
+
+def rcholqr2(X, k, seed):
+    """Alg. 3: returns (Q, R, S) -- S is the orthonormal sketch from the first pass."""
+    Q, S, R = rcholqr(X, k, seed)
+    Q2, R2, _ = cholqr_pass(Q, R)
+    return Q2, R2, S
+
+
+def reduced(X, k, seed, L=None):
+    """Alg. 5: returns (Z, S, R); L is an explicit l x m extractor, or None for L = Theta (then Z ~ S)."""
+    X = np.asarray(X, dtype=np.float64)
+    P = sketch(X, k, seed)
+    Y = P if L is None else np.asarray(L, dtype=np.float64) @ X
+    S, R = linalg.householder_qr(P)
+    Z = linalg.forward_substitution(Y, R)
+    return Z, S, R
+
+
+def rrrcholqr(X, k, seed, tau):
+    """Alg. 7 with column normalisation: returns (Q m x r, S k x r, R r x n, perm, r).
+
+    X[:, perm] ~ Q R.  Zero columns of X are left unscaled (D_j = 1 for them).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    D = column_norms(X)
+    Dsafe = np.where(D > 0, D, 1.0)
+    P = sketch(X, k, seed) / Dsafe[None, :]                  # P <- P D^{-1}
+    S, R, perm = linalg.qrcp(P)                               # step 2
+    r = linalg.truncation_rank(R, tau)                        # step 3
+    Xsel = X[:, perm[:r]] / Dsafe[perm[:r]][None, :]          # X Pi_{:,1:r} D_sel^{-1}
+    Q = linalg.forward_substitution(Xsel, R[:r, :r])          # step 4
+    Rout = R[:r, :] * Dsafe[perm][None, :]                    # step 5 and R <- R Pi^T D Pi
+    return Q, S[:, :r], Rout, perm, r
+
+
+def rrrcholqr2(X, k, seed, tau):
+    """Alg. 7 followed by one CholeskyQR pass: returns (Q, R, perm, r)."""
+    Q, _, R, perm, r = rrrcholqr(X, k, seed, tau)
+    if r == 0:
+        return Q, R, perm, r
+    Q2, R2, _ = cholqr_pass(Q, R)
+    return Q2, R2, perm, r
+
+
+# ---------------------------------------------------------------- metrics (Sec. 6)
+
+def orthogonality(Q):
+    """Delta = ||Q^T Q - I||_2."""
+    n = Q.shape[1]
+    return linalg.spectral_norm(Q.T @ Q - np.eye(n))
+
+
+def condition_number(A):
+    s = np.linalg.svd(A, compute_uv=False)
+    return float(s[0] / s[-1]) if s[-1] > 0 else np.inf
+
+
+def residuals(X, Q, R, perm=None):
+    """(||X - Q R||_F / ||X||_F, max_j ||X_j - (QR)_j|| / ||X_j||) on the columns X[:, perm]."""
+    X = np.asarray(X, dtype=np.float64)
+    if perm is not None:
+        X = X[:, perm]
+    E = X - Q @ R
+    cn = column_norms(X)
+    col = column_norms(E) / np.where(cn > 0, cn, 1.0)
+    return float(np.linalg.norm(E) / np.linalg.norm(X)), float(np.max(col))
+
+
+def embedding_epsilon(G_scaled, U):
+    """Exact epsilon of Def. 2.1 for Theta (dense, given) on range(U), U orthonormal: max |sigma_i(Theta U)^2 - 1|."""
+    s = np.linalg.svd(G_scaled @ U, compute_uv=False)
+    return float(np.max(np.abs(s * s - 1.0)))

@@ -1,0 +1,79 @@
+"""The sketching matrix Theta (Sec. 2, rescaled Gaussian OSE), realised from Philox bytes.
+
+The paper asks for a k x m oblivious subspace embedding drawn from a seeded
+generator so that it is never stored (Sec. 2, Sec. 3.1), with i.i.d. zero-mean
+entries of variance 1/k.  The realisation used here (a reading; the paper
+fixes no bit stream):
+
+* Entry (i, r) -- row i < k of Theta, global row r of X -- takes byte
+  (r mod 16) of the Philox4x32-10 output for
+      counter = (floor(r/16) mod 2^32, floor(r/16) div 2^32, i, stream),
+      key     = (seed mod 2^32, seed div 2^32),
+  byte b of the 128-bit output being bits 8*(b mod 4) .. 8*(b mod 4)+7 of
+  word floor(b/4).
+* That byte t in [0, 256) selects the level
+      T[t] = round(44 * Phi^{-1}((t + 1/2) / 256)),
+  an integer in [-127, 127]: the 256-point quantile discretisation of N(0, 1)
+  scaled by 44 (a sub-Gaussian, zero-mean, antisymmetric distribution).
+* Theta(i, r) = T[t] / sqrt(k * v) with v = (1/256) * sum_t T[t]^2, so
+  E[Theta^T Theta] = I exactly.
+
+Phi^{-1} here is scipy's ``ndtri`` (a library primitive); the library builds
+its own table with its own inverse-CDF code and the tests compare the two
+tables entry by entry.
+"""
+import numpy as np
+from scipy.special import ndtri
+
+from .philox import philox4x32_10
+
+TABLE_SCALE = 44.0
+LEVELS = 256
+
+
+def quantile_table():
+    """The 256 integer levels T[t] (float64 holding integers)."""
+    t = np.arange(LEVELS, dtype=np.float64)
+    x = TABLE_SCALE * ndtri((t + 0.5) / LEVELS)
+    # round half away from zero; no level lies within 1e-3 of a half-integer
+    return np.sign(x) * np.floor(np.abs(x) + 0.5)
+
+
+def table_variance():
+    """v = mean of T^2 (exact in FP64: an integer sum divided by 256)."""
+    T = quantile_table()
+    return float(np.sum(T * T)) / LEVELS
+
+
+def theta_scale(k):
+    """c = 1/sqrt(k v): Theta = c * (integer levels)."""
+    return 1.0 / np.sqrt(float(k) * table_variance())
+
+
+def theta_bytes(seed, k, row_offset, m, stream=0):
+    """The k x m array of Philox bytes t(i, r) for rows r = row_offset .. row_offset+m-1."""
+    if m == 0:
+        return np.zeros((k, 0), dtype=np.int64)
+    q0 = row_offset // 16
+    q1 = (row_offset + m - 1) // 16
+    q = np.arange(q0, q1 + 1, dtype=np.uint64)[None, :]          # one Philox call per 16 rows
+    i = np.arange(k, dtype=np.uint64)[:, None]
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    words = philox4x32_10(q & np.uint64(0xFFFFFFFF), q >> np.uint64(32),
+                          i, np.uint64(stream), seed & 0xFFFFFFFF, seed >> 32)
+    out = np.empty((k, q.shape[1], 16), dtype=np.int64)
+    for b in range(16):                                          # byte b of the 128-bit output
+        out[:, :, b] = ((words[b >> 2] >> np.uint64(8 * (b & 3))) & np.uint64(0xFF)).astype(np.int64)
+    out = out.reshape(k, -1)
+    start = row_offset - 16 * q0
+    return out[:, start:start + m]
+
+
+def theta_levels(seed, k, row_offset, m, stream=0):
+    """Integer levels G(i, r) = T[t(i, r)] as float64 (Theta = theta_scale(k) * G)."""
+    return quantile_table()[theta_bytes(seed, k, row_offset, m, stream)]
+
+
+def theta(seed, k, row_offset, m, stream=0):
+    """Dense Theta[:, row_offset:row_offset+m] in FP64 (for small m only)."""
+    return theta_scale(k) * theta_levels(seed, k, row_offset, m, stream)

@@ -1,0 +1,192 @@
+"""Pins for the oracle's algorithms (Alg. 2, 3, 5, 7) against special cases and Sec. 5 bounds."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import linalg, rcqr, theta
+
+U64 = np.finfo(np.float64).eps / 2
+
+
+def svd_matrix(m, n, cond, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.logspace(0, -math.log10(cond), n) if n > 1 else np.ones(1)
+    return (U * s[None, :]) @ V.T, U
+
+
+def rcholqr_violations(X, U, k, seed, kappa, Q, S, R):
+    """Violated statements of Thm. 5.2 for Alg. 2 output (empty list when all hold)."""
+    m, n = X.shape
+    bad = []
+    Th = theta.theta(seed, k, 0, m)
+    eps = rcqr.embedding_epsilon(Th, U)
+    s = np.linalg.svd(Q, compute_uv=False)
+    slack = 4 * U64 * n ** 1.5 * kappa
+    if not s.min() >= (1 + eps) ** -0.5 - slack:
+        bad.append("sigma_min")
+    if eps < 1 and not s.max() <= (1 - eps) ** -0.5 + slack:
+        bad.append("sigma_max")
+    dX = Q @ R - X
+    if not np.all(np.linalg.norm(dX, axis=0) <= 2.1 * U64 * n * np.linalg.norm(X, axis=0)):
+        bad.append("main1")
+    if not np.linalg.norm(S - Th @ Q) <= 6.1 * U64 * n ** 1.5 * kappa:
+        bad.append("main3")
+    # Householder in uniform FP64 (not the u_f << u of Assumptions 5.1): O(sqrt(k) n u)
+    if not np.linalg.norm(S.T @ S - np.eye(n)) <= 10 * math.sqrt(S.shape[0]) * n * U64:
+        bad.append("S orthonormal")
+    return bad
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e8, 1e12])
+def test_rcholqr_theorem_5_2(kappa):
+    m, n, k = 3000, 12, 192          # k = 16 n: eps < 1 so both sides of (main2) are finite
+    X, U = svd_matrix(m, n, kappa, 1)
+    Q, S, R = rcqr.rcholqr(X, k, 77)
+    assert rcholqr_violations(X, U, k, 77, kappa, Q, S, R) == []
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    m, n, k, kappa = 2000, 8, 128, 1e6
+    X, U = svd_matrix(m, n, kappa, 2)
+    good = rcqr.rcholqr(X, k, 5)
+    assert rcholqr_violations(X, U, k, 5, kappa, *good) == []
+    # wrong scale of Theta (drop the 1/sqrt(k v)): sigma(Q) leaves the Thm. 5.2 interval
+    monkeypatch.setattr(rcqr, "theta_scale", lambda kk: 1.3 / math.sqrt(kk * theta.table_variance()))
+    assert rcholqr_violations(X, U, k, 5, kappa, *rcqr.rcholqr(X, k, 5))
+    monkeypatch.undo()
+    # transposed operand in the substitution
+    real_fs = linalg.forward_substitution
+    monkeypatch.setattr(linalg, "forward_substitution", lambda A, R: real_fs(A, R.T))
+    assert rcholqr_violations(X, U, k, 5, kappa, *rcqr.rcholqr(X, k, 5))
+    monkeypatch.undo()
+    # dropped term in the substitution (the last off-diagonal contribution)
+    def fs_dropped(A, R):
+        Q = np.empty_like(A)
+        for j in range(A.shape[1]):
+            Q[:, j] = (A[:, j] - Q[:, :max(j - 1, 0)] @ R[:max(j - 1, 0), j]) / R[j, j]
+        return Q
+    monkeypatch.setattr(linalg, "forward_substitution", fs_dropped)
+    assert rcholqr_violations(X, U, k, 5, kappa, *rcqr.rcholqr(X, k, 5))
+    monkeypatch.undo()
+    # sign error in a reflector update
+    real_hqr = linalg.householder_qr
+    monkeypatch.setattr(linalg, "householder_qr", lambda P: (lambda S, R: (S, -R))(*real_hqr(P)))
+    assert rcholqr_violations(X, U, k, 5, kappa, *rcqr.rcholqr(X, k, 5))
+
+
+def test_identity_sketch_reduces_to_householder_qr():
+    # Theta = I (k = m): Alg. 2 becomes Householder QR of X itself
+    X, _ = svd_matrix(50, 7, 1e3, 3)
+    Q, S, R = rcqr.rcholqr_from_sketch(X, X)
+    Ql, Rl = np.linalg.qr(X)
+    sg = np.where(np.diag(Rl) < 0, -1.0, 1.0)
+    assert np.max(np.abs(R - Rl * sg[:, None])) < 1e-13
+    assert np.max(np.abs(Q - Ql * sg[None, :])) < 1e-12
+    assert np.max(np.abs(S - Q)) < 1e-12
+
+
+def test_single_column_closed_form():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((777, 1))
+    Q, S, R = rcqr.rcholqr(x, 16, 3)
+    P = theta.theta(3, 16, 0, 777) @ x
+    assert R[0, 0] == pytest.approx(np.linalg.norm(P), rel=1e-14)
+    assert np.allclose(Q, x / np.linalg.norm(P), rtol=1e-14, atol=0)
+
+
+def test_sketch_exact_on_integers_bruteforce():
+    rng = np.random.default_rng(9)
+    m, n, k, seed = 300, 3, 16, 1234
+    X = rng.integers(-128, 128, size=(m, n))
+    G = theta.quantile_table().astype(np.int64)[theta.theta_bytes(seed, k, 0, m)]
+    exact = [[sum(int(G[i, r]) * int(X[r, j]) for r in range(m)) for j in range(n)] for i in range(k)]
+    P = rcqr.sketch(X.astype(np.float64), k, seed)
+    assert np.array_equal(P, theta.theta_scale(k) * np.array(exact, dtype=np.float64))
+
+
+def test_sketch_is_additive_over_row_shards():
+    X, _ = svd_matrix(5000, 6, 1e2, 4)
+    P = rcqr.sketch(X, 32, 42)
+    P2 = rcqr.sketch(X[:1234], 32, 42) + rcqr.sketch(X[1234:], 32, 42, row_offset=1234)
+    assert np.max(np.abs(P - P2)) < 1e-13 * np.max(np.abs(P))
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e12])
+def test_rcholqr2_orthonormal_and_matches_householder_R(kappa):
+    m, n, k = 4000, 16, 64
+    X, _ = svd_matrix(m, n, kappa, 5)
+    Q, R, S = rcqr.rcholqr2(X, k, 11)
+    assert rcqr.orthogonality(Q) < 10 * n * U64
+    res_f, res_c = rcqr.residuals(X, Q, R)
+    assert res_f < 10 * n * U64 and res_c < 10 * n * U64
+    _, Rh = np.linalg.qr(X)
+    Rh *= np.where(np.diag(Rh) < 0, -1.0, 1.0)[:, None]
+    # the R of an orthonormal-Q factorization is unique: pass 2 recovers Householder's R
+    assert np.max(np.abs(R - Rh) / np.abs(Rh).max(axis=0)[None, :]) < 10 * n * U64 * (1 + kappa * U64 * 1e3)
+
+
+def test_reduced_with_theta_returns_sketch_of_Q():
+    m, n, k, kappa = 3000, 10, 160, 1e6
+    X, U = svd_matrix(m, n, kappa, 6)
+    Z, S, R = rcqr.reduced(X, k, 21)
+    Q, S1, R1 = rcqr.rcholqr(X, k, 21)
+    assert np.array_equal(S, S1) and np.array_equal(R, R1)
+    # Z = P R^{-1} is the sketch of Q; it equals S up to Thm. 5.4-size rounding
+    assert np.linalg.norm(Z - S) <= 6.1 * U64 * n ** 1.5 * kappa
+    Th = theta.theta(21, k, 0, m)
+    assert np.linalg.norm(Z - Th @ Q) <= 6.1 * U64 * n ** 1.5 * kappa
+
+
+def test_reduced_with_explicit_extractor_rows():
+    m, n, k, l, kappa = 2000, 8, 128, 5, 1e5
+    X, _ = svd_matrix(m, n, kappa, 7)
+    L = np.random.default_rng(1).standard_normal((l, m))
+    Z, S, R = rcqr.reduced(X, k, 3, L=L)
+    Q, _, _ = rcqr.rcholqr(X, k, 3)
+    # Thm. 5.4 first bound: ||Z_i - L_i Q|| <= 3.5 u n^{3/2} kappa ||L_i||
+    err = np.linalg.norm(Z - L @ Q, axis=1)
+    assert np.all(err <= 3.5 * U64 * n ** 1.5 * kappa * np.linalg.norm(L, axis=1))
+
+
+def test_rrrcholqr_planted_rank_and_theorem_5_7():
+    rng = np.random.default_rng(12)
+    m, n, r, k = 3000, 16, 8, 64
+    B = rng.standard_normal((m, r)) * rng.uniform(0.1, 10, size=r)[None, :]
+    X = np.hstack([B, B @ rng.standard_normal((r, n - r)) + 1e-12 * rng.standard_normal((m, n - r))])
+    tau = 1e-8
+    Q, S, R, perm, rr = rcqr.rrrcholqr(X, k, 5, tau)
+    assert rr == r
+    assert sorted(perm.tolist()) == list(range(n))
+    # Thm. 5.7: column-normalised residual <= 2 tau (up to rounding), Q well conditioned
+    D = rcqr.column_norms(X)
+    E = (X[:, perm] - Q @ R) / D[perm][None, :]
+    assert np.linalg.norm(E) <= 2 * tau + 1e-13
+    Th = theta.theta(5, k, 0, m)
+    Uq, _ = np.linalg.qr(Q)
+    eps = rcqr.embedding_epsilon(Th, Uq)
+    s = np.linalg.svd(Q, compute_uv=False)
+    assert s.min() >= (1 + eps) ** -0.5 - 0.016
+    if eps < 1:
+        assert s.max() <= (1 - eps) ** -0.5 + 0.016
+    assert np.linalg.norm(S - Th @ Q) <= 0.061
+    Q2, R2, perm2, r2 = rcqr.rrrcholqr2(X, k, 5, tau)
+    assert r2 == r and np.array_equal(perm2, perm)
+    assert rcqr.orthogonality(Q2) < 100 * U64 * n
+
+
+def test_rrrcholqr_full_rank_is_permuted_rcholqr():
+    X, _ = svd_matrix(1500, 6, 1e3, 13)
+    Q, S, R, perm, r = rcqr.rrrcholqr(X, 48, 9, 1e-15)
+    assert r == 6
+    res_f, res_c = rcqr.residuals(X, Q, R, perm)
+    assert res_c < 50 * U64 * 6
+
+
+def test_cholqr_pass_reports_indefinite_gram():
+    Q = np.ones((4, 2))                                   # Gram [[4,4],[4,4]]: second pivot is exactly 0
+    with pytest.raises(linalg.NotSPD) as e:
+        rcqr.cholqr_pass(Q, np.eye(2))
+    assert e.value.j == 1
