@@ -1,0 +1,299 @@
+"""Benchmark: GB/s of X factored by RCholeskyQR2 on one GB300 (and N replicas under torchrun).
+
+Workload (the paper's first test family, Sec. 6.1 / 6.3, at the size of the
+headline configuration): X = U diag(sigma) V^T, 4,194,304 x 64, sigma
+log-spaced from 1 to 1e-8 (cond 1e8), Gaussian sketch with k = 256,
+column-major with ld = m, RCholeskyQR2 (Alg. 3).  The headline ``value`` is
+the mixed path (X stored FP32: exact sketch, FP64 small factorizations, FP32
+output Q); the FP64 path (X and Q in FP64) is measured on the same matrix and
+reported beside it.  Inputs are larger than L2 (1.07 GB / 2.15 GB), so no
+flush is needed between steps.
+
+--impl reference times the CPU FP64 oracle on a bounded row sample of the
+same workload (the slow baseline; the oracle is test infrastructure that only
+this arm, the cpu_baseline field and the tests execute).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, K, COND = 4194304, 64, 256, 1e8
+SEED_X, SEED_THETA = 1002, 0x5EED0002
+ORACLE_ROWS = 1 << 19          # bounded sample for the CPU oracle (about 10-30 s of work)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=M)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
+    p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline oracle timing")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_time(m_rows, n=N, k=K, dtype="f32"):
+    """Time the CPU oracle's RCholeskyQR2 on the first m_rows rows of the workload family."""
+    import numpy as np
+    import torch
+    from paper_2210_09953_gb300 import inputs
+    from oracle import rcqr as orc
+    X = inputs.svd_matrix(m_rows, n, COND, SEED_X, dtype=dtype, device="cpu")
+    Xh = X.to(torch.float64).numpy()
+    t0 = time.perf_counter()
+    Q, R, _ = orc.rcholqr2(Xh, k, SEED_THETA)
+    dt = time.perf_counter() - t0
+    bytes_x = m_rows * n * (4 if dtype == "f32" else 8)
+    return bytes_x / dt / 1e9, dt, float(orc.orthogonality(Q))
+
+
+def cpu_baseline_record(m_rows):
+    gbs, dt, orth = oracle_time(m_rows)
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"RCholeskyQR2 of the first {m_rows} rows (x{N}, FP32-stored, cond 1e8, k={K}) in "
+                      f"{dt:.1f} s, numpy FP64 with its default BLAS threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_time(ORACLE_ROWS // 4)
+    for _ in range(args.steps):
+        gbs, dt, _ = oracle_time(ORACLE_ROWS // 4)
+        vals.append(gbs)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "GB/s of X factored (RCholeskyQR2, cond 1e8)", "value": round(v, 4),
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"rcholqr2 {args.m}x{N} f32-stored cond 1e8 k={K}", "sample_rows": ORACLE_ROWS // 4},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"first {ORACLE_ROWS // 4} rows per step"},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7 and parts[0].isdigit():
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[0]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][1]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_09953_gb300 import _binding as rc
+    from paper_2210_09953_gb300 import inputs
+
+    m = args.m
+    # replicas: every rank factors its own matrix (weak scaling, no collective on the data path)
+    X64 = inputs.svd_matrix(m, N, COND, SEED_X + rank, dtype="f64", device=dev)
+    X32 = X64.to(torch.float32).t().contiguous().t()
+    stream = torch.cuda.current_stream()
+
+    def make_buffers(X):
+        prec = rc.prec_of(X.dtype)
+        qdt = torch.float64 if prec == rc.F64 else torch.float32
+        Q = rc.colmajor(m, N, qdt, dev)
+        ws = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.DIRECT2, prec) + 256, dtype=torch.uint8, device=dev)
+        return Q, ws
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            fn()
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end) / steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t[0])
+        return ms
+
+    Q32, ws32 = make_buffers(X32)
+
+    def step32():
+        rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32)
+
+    with Clocks(local) as clk:
+        ms32 = timed(step32, args.steps, args.warmup)
+    clocks = clk.summary()
+    Q, R, _, _, status = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32)
+    torch.cuda.synchronize()
+    ok32 = int(status[0]) == 0
+    G = (Q.double().t() @ Q.double())
+    orth32 = float(torch.linalg.matrix_norm(G - torch.eye(N, dtype=torch.float64, device=dev), ord=2))
+    res32 = float(torch.linalg.norm(Q.double() @ R - X32.double()) / torch.linalg.norm(X32.double()))
+    bytes32 = m * N * 4
+    value = world * bytes32 / (ms32 * 1e-3) / 1e9
+
+    # dominant kernel: the sketch (Alg. 2 step 1), timed alone on the same stream
+    P = rc.colmajor(K, N, torch.float64, dev)
+    ms_sketch = timed(lambda: rc.rcqr_sketch(X32, K, SEED_THETA, P=P, workspace=ws32), max(3, args.steps), 2)
+    R1 = rc.rcqr_small_qr(P, want_S=False)
+    ms_trsm = timed(lambda: rc.rcqr_trsm(X32, R1, Q=Q32), max(3, args.steps), 2)
+
+    fp64 = None
+    if not args.no_fp64:
+        Q64, ws64 = make_buffers(X64)
+
+        def step64():
+            rc.rcqr_factor(X64, K, SEED_THETA, variant=rc.DIRECT2, Q=Q64, workspace=ws64)
+        ms64 = timed(step64, max(1, min(args.steps, 3)), 1)
+        Qd, Rd, _, _, st64 = rc.rcqr_factor(X64, K, SEED_THETA, variant=rc.DIRECT2, Q=Q64, workspace=ws64)
+        torch.cuda.synchronize()
+        Gd = Qd.t() @ Qd
+        fp64 = {"value": round(world * m * N * 8 / (ms64 * 1e-3) / 1e9, 3), "unit": "GB/s",
+                "ms_per_step": round(ms64, 3),
+                "orth": float(torch.linalg.matrix_norm(Gd - torch.eye(N, dtype=torch.float64, device=dev), ord=2)),
+                "status": int(st64[0])}
+        del Q64, ws64
+
+    # end to end through the public call: pinned host X -> device, factor, Q and R back to host
+    Xh = torch.empty((N, m), dtype=torch.float32, pin_memory=True).t()
+    Xh.copy_(X32)
+    Qh = torch.empty((N, m), dtype=torch.float32, pin_memory=True).t()
+    Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
+    Xd = rc.colmajor(m, N, torch.float32, dev)
+
+    def step_e2e():
+        Xd.copy_(Xh, non_blocking=True)
+        Qd_, Rd_, _, _, _ = rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32)
+        Qh.copy_(Qd_, non_blocking=True)
+        Rh.copy_(Rd_, non_blocking=True)
+    ms_e2e = timed(step_e2e, max(3, min(args.steps, 5)), 1)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sketch_bytes = m * N * 4                 # algorithmic: X read once
+    achieved = sketch_bytes / (ms_sketch * 1e-3) / 1e9
+    launches_per_step = 10                   # reset, sketch x2, small QR, rank, TRSM, Gram x2, Cholesky, TRSM
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            cpu = cpu_baseline_record(ORACLE_ROWS)
+        line = {
+            "metric": "GB/s of X factored (RCholeskyQR2, mixed path: FP32 X) at stated ||Q^TQ-I||",
+            "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms32, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 storage / f64 sketch and small ops",
+            "data": "synthetic",
+            "config": {"workload": f"rcholqr2 {m}x{N} k={K} cond 1e8 (U diag(sigma) V^T), X f32 column-major",
+                       "seed_theta": SEED_THETA, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy": {"orth_QtQ_minus_I": orth32, "residual_rel_F": res32, "status_ok": ok32},
+            "fp64_path": fp64,
+            "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4)},
+            "roofline": {"kernel": "sketch (Theta X, FP32 X)", "bound": "hbm", "achieved": round(achieved, 2),
+                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                         "peak_source": peak_src},
+            "clocks": clocks,
+            "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
+                    "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8},
+            "gpu_launches": launches_per_step * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * rcqr.h -- C ABI of librcqr.so: randomized Cholesky QR of a tall-skinny matrix
+ * on one GB300 (sm_103a).
+ *
+ * Method: O. Balabanov, "Randomized Cholesky QR factorizations" (arXiv 2210.09953).
+ * The problem (Sec. 1): X (m x n, n << m) = Q R with R upper triangular (or
+ * trapezoidal, with permuted columns) and Q well conditioned or orthonormal.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major: element (i, j) of A lives at A[i + j * lda].
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *     comment says "host".  The library never allocates device memory, never
+ *     frees caller memory and never synchronises the stream: scratch space is
+ *     the caller's `workspace` (at least rcqr_workspace_size() bytes, 256-byte
+ *     aligned), and all work is queued on `stream` in order.
+ *   - Argument errors are returned synchronously (RCQR_EINVAL, RCQR_EWORKSPACE,
+ *     RCQR_EUNSUPPORTED) before anything is queued.  A CUDA launch error gives
+ *     RCQR_ECUDA.  Numerical failures found on the device (a Cholesky pivot
+ *     <= 0, a zero sketch) are written to `dev_status` (device int[2]: status
+ *     code, then the failing pivot index or -1), which the caller reads after
+ *     synchronising; the entry points that take `dev_status` reset it first.
+ *   - Theta (Sec. 2) is never stored.  Entry (i, r) of the k x m sketching
+ *     matrix -- i < k, r the global row index of X -- is T[t] / sqrt(k v): t is
+ *     byte (r mod 16) of Philox4x32-10(counter = (floor(r/16) mod 2^32,
+ *     floor(r/16) div 2^32, i, stream), key = (seed mod 2^32, seed div 2^32)),
+ *     T[t] = round(44 Phi^{-1}((t + 1/2)/256)) in [-127, 127] (the 256-point
+ *     quantile grid of N(0,1)), v = (1/256) sum_t T[t]^2.  stream = 0 except in
+ *     the batched call, where it is the problem index.
+ *   - Precision `prec`: RCQR_F64 (X and Q are double), RCQR_F32 (X and Q are
+ *     float), RCQR_BF16 (X is bfloat16, Q is float).  R, P, S, Z are always
+ *     double.  The sketch and the small factorizations run in FP64-level
+ *     precision for every prec (the multi-precision model of Sec. 1.3 and Sec. 5:
+ *     the minor operations in higher precision).
+ *   - Limits: 1 <= n <= 256, n <= k <= 2048, k a multiple of 8, m >= 1,
+ *     ld >= m, 0 <= row_offset.
+ */
+#ifndef RCQR_H
+#define RCQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+  RCQR_OK = 0,
+  RCQR_EINVAL = -1,       /* bad argument (sizes, leading dimensions, null pointer) */
+  RCQR_ENOTSPD = -2,      /* device: Cholesky pivot <= 0 in the CholeskyQR pass (Alg. 3 step 3) */
+  RCQR_ERANK0 = -3,       /* device: the sketch is zero, no column can be kept (Alg. 7 step 3) */
+  RCQR_ECUDA = -4,        /* a CUDA call failed */
+  RCQR_ETIMEOUT = -5,     /* device: a bounded wait inside a kernel gave up */
+  RCQR_EWORKSPACE = -6,   /* workspace missing, too small or misaligned */
+  RCQR_EUNSUPPORTED = -7  /* valid request this build does not support (e.g. no sm_103a device) */
+} rcqr_status;
+
+typedef enum {
+  RCQR_DIRECT = 0,   /* RCholeskyQR, Alg. 2: Q well conditioned */
+  RCQR_DIRECT2 = 1,  /* RCholeskyQR2, Alg. 3: Q orthonormal */
+  RCQR_RR = 2,       /* RRRCholQR, Alg. 7 with the column normalisation of Sec. 4 */
+  RCQR_RR2 = 3       /* RRRCholQR followed by one CholeskyQR pass (Sec. 4) */
+} rcqr_variant;
+
+typedef enum { RCQR_F64 = 0, RCQR_F32 = 1, RCQR_BF16 = 2 } rcqr_prec;
+
+/* Human-readable name of a status code (static string). */
+const char *rcqr_status_string(int status);
+
+/* Bytes of workspace rcqr_factor / rcqr_reduced / rcqr_sketch need for these
+ * sizes (an upper bound valid for all three). 0 on invalid sizes. */
+size_t rcqr_workspace_size(int64_t m, int64_t n, int64_t k, int variant, int prec);
+
+/* Host: write the 256 integer levels T[t] of Theta (see above) to out[0..255].
+ * Returns RCQR_OK. */
+int rcqr_theta_table(int32_t *out);
+
+/* Host: the scale c = 1/sqrt(k v) so that Theta = c * T[t]. */
+double rcqr_theta_scale(int64_t k);
+
+/* Sketch, Alg. 2 step 1 (Sec. 3.1: one pass over X, "a simple addition" as the
+ * reduction):  P = Theta X  (k x n, double, ldp >= k), Theta's columns taken at
+ * global rows row_offset .. row_offset+m-1, so sketches of row blocks of a
+ * larger matrix add up to the sketch of the whole (the shard API).
+ * colnorm2 (nullable, double[n]) receives the squared column norms of X
+ * (the matrix D^2 of Sec. 4). */
+rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                        int64_t k, uint64_t seed, int64_t row_offset,
+                        double *P, int64_t ldp, double *colnorm2,
+                        void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Householder QR of a small k x n double matrix (Alg. 2 step 2, Sec. 3.1):
+ * P = S R with S (k x n, orthonormal columns, nullable) and R (n x n, upper,
+ * diag(R) >= 0, strictly lower part set to 0). */
+rcqr_status rcqr_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp,
+                          double *S, int64_t lds, double *R, int64_t ldr,
+                          void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Column-pivoted Householder QR of P D^{-1} and the truncation rank (Alg. 7
+ * steps 2-3, column normalisation of Sec. 4):  (P D^{-1})[:, perm] = S R,
+ * D = diag(sqrt(colnorm2)) (colnorm2 nullable: D = I), pivot = the largest
+ * recomputed remaining column norm, ties to the lowest index;
+ * rank = min r with ||R[r:, r:]||_F <= tau ||R||_2; then R is overwritten by
+ * R[:rank, :] Pi^T D Pi (rows >= rank set to 0).  perm: device int32[n];
+ * rank: device int64.  dev_status gets RCQR_ERANK0 if rank = 0. */
+rcqr_status rcqr_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp,
+                      const double *colnorm2, double tau,
+                      double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                      void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
+/* Forward substitution, Alg. 2 step 3:  Q = X R^{-1} (m x n; Q's type follows
+ * prec: double for F64, float otherwise).  R is n x n upper with nonzero
+ * diagonal.  perm (nullable device int32[n]) and rank (nullable device int64):
+ * when given, the input columns are X[:, perm[j]] for j < rank and Q's columns
+ * j >= rank are set to 0 (the RR form of Alg. 7 step 4).  Q may alias X only
+ * when perm is NULL and the types match. */
+rcqr_status rcqr_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                      const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
+                      void *Q, int64_t ldq, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Gram matrix, Alg. 3 step 2:  A = Q^T Q (n x n double, both triangles), Q of
+ * type double (F64) or float (F32, BF16). rank (nullable): only the leading
+ * rank x rank block is formed, the rest set to 0. */
+rcqr_status rcqr_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
+                      const int64_t *rank, double *A, int64_t lda,
+                      void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* CholeskyQR update, Alg. 3 step 3:  R' = chol(A) (upper, positive diagonal),
+ * R <- R' R.  R' is written to Rp (n x n, strictly lower part 0).  rank
+ * (nullable): only the leading rank x rank block of A and rank rows of R are
+ * used.  A pivot <= 0 sets dev_status = {RCQR_ENOTSPD, j} and leaves R as it was. */
+rcqr_status rcqr_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
+                             double *Rp, int64_t ldrp, double *R, int64_t ldr,
+                             int *dev_status, cudaStream_t stream);
+
+/* The factorization (Alg. 2, 3, 7 and RRRCholQR2).
+ * X: m x n (type by prec), Q: m x n (m x rank for RR; columns >= rank zeroed),
+ * R: n x n double (RR: rows >= rank zeroed; X[:, perm] = Q R), perm: device
+ * int32[n] (RR only, else nullable), rank: device int64 (nullable; n for the
+ * direct variants).  tau: truncation tolerance of Alg. 7 step 3 (RR only).
+ * Q may alias X for RCQR_DIRECT / RCQR_DIRECT2 when the types match. */
+rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                        int64_t k, uint64_t seed, int variant, double tau,
+                        void *Q, int64_t ldq, double *R, int64_t ldr,
+                        int32_t *perm, int64_t *rank,
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
+/* Reduced RCholeskyQR, Alg. 5:  P = Theta X, Y = L X, [S, R] = QR(P),
+ * Z = Y R^{-1}.  L: l x m double extractor (ldl >= l), or NULL for L = Theta
+ * (then l must equal k and Z = P R^{-1}, the sketch of Q).  Z: l x n,
+ * S: k x n (nullable), R: n x n. */
+rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                         int64_t k, uint64_t seed, const double *L, int64_t l, int64_t ldl,
+                         double *Z, int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
+                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCQR_H */

@@ -38,6 +38,18 @@ def sketch(X, k, seed, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK):
     return theta_scale(k) * acc
 
 
+def sketch_rows(X, k, seed, rows, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK):
+    """Selected rows of P = Theta X (one output row at a time for sampled checks of long X)."""
+    X = np.asarray(X)
+    m, n = X.shape
+    acc = np.zeros((len(rows), n))
+    for r0 in range(0, m, row_block):
+        r1 = min(m, r0 + row_block)
+        G = theta_levels(seed, k, row_offset + r0, r1 - r0, stream, rows=rows)
+        acc += G @ np.asarray(X[r0:r1], dtype=np.float64)
+    return theta_scale(k) * acc
+
+
 def column_norms(X):
     """D_j = ||X_(:,j)||_2 (Sec. 4, the normalisation matrix)."""
     X = np.asarray(X, dtype=np.float64)

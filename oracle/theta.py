@@ -50,14 +50,20 @@ def theta_scale(k):
     return 1.0 / np.sqrt(float(k) * table_variance())
 
 
-def theta_bytes(seed, k, row_offset, m, stream=0):
-    """The k x m array of Philox bytes t(i, r) for rows r = row_offset .. row_offset+m-1."""
+def theta_bytes(seed, k, row_offset, m, stream=0, rows=None):
+    """The k x m array of Philox bytes t(i, r) for rows r = row_offset .. row_offset+m-1.
+
+    ``rows`` (optional) selects Theta's rows i (default 0..k-1); the result then
+    has one line per selected row.
+    """
+    sel = np.arange(k) if rows is None else np.asarray(rows)
     if m == 0:
-        return np.zeros((k, 0), dtype=np.int64)
+        return np.zeros((len(sel), 0), dtype=np.int64)
+    k = len(sel)
     q0 = row_offset // 16
     q1 = (row_offset + m - 1) // 16
     q = np.arange(q0, q1 + 1, dtype=np.uint64)[None, :]          # one Philox call per 16 rows
-    i = np.arange(k, dtype=np.uint64)[:, None]
+    i = sel.astype(np.uint64)[:, None]
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     words = philox4x32_10(q & np.uint64(0xFFFFFFFF), q >> np.uint64(32),
                           i, np.uint64(stream), seed & 0xFFFFFFFF, seed >> 32)
@@ -69,9 +75,9 @@ def theta_bytes(seed, k, row_offset, m, stream=0):
     return out[:, start:start + m]
 
 
-def theta_levels(seed, k, row_offset, m, stream=0):
+def theta_levels(seed, k, row_offset, m, stream=0, rows=None):
     """Integer levels G(i, r) = T[t(i, r)] as float64 (Theta = theta_scale(k) * G)."""
-    return quantile_table()[theta_bytes(seed, k, row_offset, m, stream)]
+    return quantile_table()[theta_bytes(seed, k, row_offset, m, stream, rows)]
 
 
 def theta(seed, k, row_offset, m, stream=0):

@@ -1,0 +1,216 @@
+"""ctypes binding of librcqr.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and takes
+torch tensors for the device arrays; it passes their data pointers, the
+caller's current CUDA stream and a workspace tensor, and raises RcqrError on
+a non-OK status.  No arithmetic of the method happens here: every step runs
+in the CUDA kernels of the library.  Importing this module loads the library
+and fails loudly if it is missing or was not built.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librcqr.so")
+
+F64, F32, BF16 = 0, 1, 2
+DIRECT, DIRECT2, RR, RR2 = 0, 1, 2, 3
+STATUS_NAMES = {0: "RCQR_OK", -1: "RCQR_EINVAL", -2: "RCQR_ENOTSPD", -3: "RCQR_ERANK0",
+                -4: "RCQR_ECUDA", -5: "RCQR_ETIMEOUT", -6: "RCQR_EWORKSPACE", -7: "RCQR_EUNSUPPORTED"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2210_09953_gb300.build`")
+lib = ctypes.CDLL(LIB_PATH)
+
+_i64, _u64, _i32, _dbl, _vp, _sz = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t)
+
+_SIGS = {
+    "rcqr_status_string": (ctypes.c_char_p, [_i32]),
+    "rcqr_workspace_size": (_sz, [_i64, _i64, _i64, _i32, _i32]),
+    "rcqr_theta_table": (_i32, [_vp]),
+    "rcqr_theta_scale": (_dbl, [_i64]),
+    "rcqr_sketch": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rcqr_small_qr": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
+    "rcqr_qrcp": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rcqr_trsm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rcqr_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rcqr_chol_update": (_i32, [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "rcqr_factor": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _dbl, _vp, _i64, _vp, _i64,
+                           _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rcqr_reduced": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _vp, _i64, _i64, _vp, _i64, _vp,
+                            _i64, _vp, _i64, _vp, _sz, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class RcqrError(RuntimeError):
+    def __init__(self, func, status):
+        super().__init__(f"{func} returned {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+def _check(func, status):
+    if status != 0:
+        raise RcqrError(func, status)
+
+
+def prec_of(dtype):
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[dtype]
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ld(t):
+    """Leading dimension of a column-major (m, n) tensor (stride (1, ld))."""
+    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[0] > 1):
+        raise ValueError("expected a column-major (m, n) tensor with stride (1, ld)")
+    return t.stride(1) if t.shape[1] > 1 else max(t.shape[0], 1)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes, device):
+    n = max(int(nbytes), 1)
+    return torch.empty(n + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned_ptr(ws):
+    p = ws.data_ptr()
+    return ctypes.c_void_p((p + 255) & ~255), ws.numel() - ((-p) % 256) - 1
+
+
+def status_string(s):
+    return lib.rcqr_status_string(s).decode()
+
+
+def rcqr_workspace_size(m, n, k, variant=DIRECT, prec=F64):
+    return int(lib.rcqr_workspace_size(m, n, k, variant, prec))
+
+
+def rcqr_theta_table():
+    out = (ctypes.c_int32 * 256)()
+    _check("rcqr_theta_table", lib.rcqr_theta_table(ctypes.cast(out, ctypes.c_void_p)))
+    return [int(v) for v in out]
+
+
+def rcqr_theta_scale(k):
+    return float(lib.rcqr_theta_scale(k))
+
+
+def colmajor(m, n, dtype, device, ld=None):
+    ld = m if ld is None else ld
+    return torch.empty((n, ld), dtype=dtype, device=device).t()[:m, :]
+
+
+def rcqr_sketch(X, k, seed, row_offset=0, P=None, colnorm2=None, workspace=None):
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    if P is None:
+        P = colmajor(k, n, torch.float64, X.device)
+    ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, DIRECT, prec), X.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_sketch", lib.rcqr_sketch(_ptr(X), m, n, _ld(X), prec, k, seed, row_offset, _ptr(P), _ld(P),
+                                          _ptr(colnorm2), wp, wb, _stream()))
+    return P
+
+
+def rcqr_small_qr(P, want_S=True):
+    k, n = P.shape
+    R = colmajor(n, n, torch.float64, P.device)
+    S = colmajor(k, n, torch.float64, P.device) if want_S else None
+    ws = _workspace(rcqr_workspace_size(max(k, 8), n, max(8, (k + 7) // 8 * 8), DIRECT, F64), P.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_small_qr", lib.rcqr_small_qr(_ptr(P), k, n, _ld(P), _ptr(S), _ld(S) if S is not None else 0,
+                                              _ptr(R), _ld(R), wp, wb, _stream()))
+    return (S, R) if want_S else R
+
+
+def rcqr_qrcp(P, tau, colnorm2=None):
+    k, n = P.shape
+    R = colmajor(n, n, torch.float64, P.device)
+    perm = torch.empty(n, dtype=torch.int32, device=P.device)
+    rank = torch.empty(1, dtype=torch.int64, device=P.device)
+    status = torch.zeros(2, dtype=torch.int32, device=P.device)
+    ws = _workspace(rcqr_workspace_size(max(k, 8), n, max(8, (k + 7) // 8 * 8), DIRECT, F64), P.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_qrcp", lib.rcqr_qrcp(_ptr(P), k, n, _ld(P), _ptr(colnorm2), float(tau), _ptr(R), _ld(R),
+                                      _ptr(perm), _ptr(rank), wp, wb, _ptr(status), _stream()))
+    return R, perm, rank, status
+
+
+def rcqr_trsm(X, R, perm=None, rank=None, Q=None):
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    if Q is None:
+        Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, X.device)
+    _check("rcqr_trsm", lib.rcqr_trsm(_ptr(X), m, n, _ld(X), prec, _ptr(R), _ld(R), _ptr(perm), _ptr(rank),
+                                      _ptr(Q), _ld(Q), None, 0, _stream()))
+    return Q
+
+
+def rcqr_gram(Q, rank=None):
+    m, n = Q.shape
+    prec = prec_of(Q.dtype)
+    A = colmajor(n, n, torch.float64, Q.device)
+    ws = _workspace(rcqr_workspace_size(m, n, max(8, (n + 7) // 8 * 8), DIRECT, prec), Q.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_gram", lib.rcqr_gram(_ptr(Q), m, n, _ld(Q), prec, _ptr(rank), _ptr(A), _ld(A), wp, wb,
+                                      _stream()))
+    return A
+
+
+def rcqr_chol_update(A, R, rank=None):
+    n = A.shape[0]
+    Rp = colmajor(n, n, torch.float64, A.device)
+    status = torch.zeros(2, dtype=torch.int32, device=A.device)
+    _check("rcqr_chol_update", lib.rcqr_chol_update(_ptr(A), n, _ld(A), _ptr(rank), _ptr(Rp), _ld(Rp),
+                                                    _ptr(R), _ld(R), _ptr(status), _stream()))
+    return Rp, status
+
+
+def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None):
+    """Returns (Q, R, perm, rank, status); perm is None for the direct variants."""
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    dev = X.device
+    if Q is None:
+        Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, dev)
+    R = colmajor(n, n, torch.float64, dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev) if variant in (RR, RR2) else None
+    rank = torch.empty(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, variant, prec), dev)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_factor", lib.rcqr_factor(_ptr(X), m, n, _ld(X), prec, k, seed, variant, float(tau), _ptr(Q),
+                                          _ld(Q), _ptr(R), _ld(R), _ptr(perm), _ptr(rank), wp, wb, _ptr(status),
+                                          _stream()))
+    return Q, R, perm, rank, status
+
+
+def rcqr_reduced(X, k, seed, L=None, want_S=True):
+    """Returns (Z, S, R, status); L (l x m, float64, column-major) or None for L = Theta."""
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    dev = X.device
+    l = k if L is None else L.shape[0]
+    Z = colmajor(l, n, torch.float64, dev)
+    S = colmajor(k, n, torch.float64, dev) if want_S else None
+    R = colmajor(n, n, torch.float64, dev)
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    ws = _workspace(rcqr_workspace_size(m, n, k, DIRECT, prec) + (l * n * 8 + 512), dev)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_reduced", lib.rcqr_reduced(_ptr(X), m, n, _ld(X), prec, k, seed, _ptr(L), l,
+                                            _ld(L) if L is not None else 0, _ptr(Z), _ld(Z), _ptr(S),
+                                            _ld(S) if S is not None else 0, _ptr(R), _ld(R), wp, wb,
+                                            _ptr(status), _stream()))
+    return Z, S, R, status

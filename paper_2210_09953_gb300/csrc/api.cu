@@ -1,0 +1,289 @@
+// The C ABI of librcqr.so (declared in include/rcqr.h): argument checks,
+// workspace layout and the stream-ordered sequence of kernels for each
+// variant of the method.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "rcqr_internal.h"
+
+namespace rcqr {
+
+int num_sms() {
+  static int count[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (count[dev] == 0) {
+    int c = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+      c = 148;
+    count[dev] = c;
+  }
+  return count[dev];
+}
+
+namespace {
+
+bool valid_prec(int prec) { return prec == RCQR_F64 || prec == RCQR_F32 || prec == RCQR_BF16; }
+
+bool valid_sizes(int64_t m, int64_t n, int64_t k) {
+  return m >= 1 && n >= 1 && n <= 256 && k >= n && k <= 2048 && (k % 8) == 0;
+}
+
+bool aligned(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+rcqr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RCQR_OK;
+  if (e == cudaErrorMemoryAllocation) return RCQR_EWORKSPACE;
+  return RCQR_ECUDA;
+}
+
+// Workspace layout of rcqr_factor (the measuring pass uses the same code).
+struct FactorBuffers {
+  double *P, *R0, *A, *Rp, *colnorm2;
+  int64_t *rank_tmp;
+};
+
+bool take_factor_buffers(Workspace &w, int64_t n, int64_t k, FactorBuffers &b) {
+  b.P = w.take<double>((size_t)k * n);
+  b.R0 = w.take<double>((size_t)n * n);
+  b.A = w.take<double>((size_t)n * n);
+  b.Rp = w.take<double>((size_t)n * n);
+  b.colnorm2 = w.take<double>((size_t)n);
+  b.rank_tmp = w.take<int64_t>(1);
+  return w.ok();
+}
+
+size_t stage_workspace(int64_t m, int64_t n, int64_t k, int prec) {
+  size_t s = sketch_workspace(m, n, k, 0, prec);
+  s = std::max(s, small_qr_workspace(k, n));
+  s = std::max(s, gram_workspace(m, n));
+  s = std::max(s, trsm_workspace(m, n, prec));
+  s = std::max(s, (size_t)n * n * 8 + 256);
+  return s;
+}
+
+}  // namespace
+}  // namespace rcqr
+
+using namespace rcqr;
+
+extern "C" {
+
+const char *rcqr_status_string(int s) {
+  switch (s) {
+    case RCQR_OK: return "RCQR_OK";
+    case RCQR_EINVAL: return "RCQR_EINVAL: invalid argument";
+    case RCQR_ENOTSPD: return "RCQR_ENOTSPD: Cholesky pivot <= 0 in the CholeskyQR pass";
+    case RCQR_ERANK0: return "RCQR_ERANK0: zero sketch, rank 0";
+    case RCQR_ECUDA: return "RCQR_ECUDA: CUDA error";
+    case RCQR_ETIMEOUT: return "RCQR_ETIMEOUT: bounded device wait expired";
+    case RCQR_EWORKSPACE: return "RCQR_EWORKSPACE: workspace missing, too small or misaligned";
+    case RCQR_EUNSUPPORTED: return "RCQR_EUNSUPPORTED: unsupported request";
+    default: return "unknown rcqr status";
+  }
+}
+
+int rcqr_theta_table(int32_t *out) {
+  if (!out) return RCQR_EINVAL;
+  const ThetaTable &t = theta_table();
+  for (int i = 0; i < 256; ++i) out[i] = t.level[i];
+  return RCQR_OK;
+}
+
+double rcqr_theta_scale(int64_t k) { return k > 0 ? theta_scale(k) : 0.0; }
+
+size_t rcqr_workspace_size(int64_t m, int64_t n, int64_t k, int variant, int prec) {
+  if (!valid_sizes(m, n, k) || !valid_prec(prec) || variant < 0 || variant > 3) return 0;
+  Workspace w(nullptr, 0);
+  FactorBuffers b;
+  take_factor_buffers(w, n, k, b);
+  const size_t fixed = w.used;
+  size_t extra = stage_workspace(m, n, k, prec);
+  extra = std::max(extra, dense_left_workspace(std::max<int64_t>(k, 1), m, n));
+  return ((fixed + 255) & ~size_t(255)) + extra + 512;
+}
+
+rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                        uint64_t seed, int64_t row_offset, double *P, int64_t ldp,
+                        double *colnorm2, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!X || !P || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m || ldp < k ||
+      row_offset < 0)
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < sketch_workspace(m, n, k, row_offset, prec))
+    return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(
+      launch_sketch(X, m, n, ldx, prec, k, seed, 0, row_offset, P, ldp, colnorm2, w, stream));
+}
+
+rcqr_status rcqr_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, double *S,
+                          int64_t lds, double *R, int64_t ldr, void *workspace, size_t ws_bytes,
+                          cudaStream_t stream) {
+  if (!P || !R || n < 1 || n > 256 || k < n || k > 2048 || ldp < k || ldr < n || (S && lds < k))
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < small_qr_workspace(k, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_small_qr(P, k, n, ldp, S, lds, R, ldr, w, stream));
+}
+
+rcqr_status rcqr_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
+                      double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                      void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  if (!P || !R || !perm || !rank || n < 1 || n > 256 || k < n || k > 2048 || ldp < k || ldr < n ||
+      !(tau >= 0.0))
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < small_qr_workspace(k, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  if (dev_status) {
+    rcqr_status s = cuda_status(launch_reset_status(dev_status, stream));
+    if (s != RCQR_OK) return s;
+  }
+  return cuda_status(
+      launch_qrcp(P, k, n, ldp, colnorm2, tau, R, ldr, perm, rank, dev_status, w, stream));
+}
+
+rcqr_status rcqr_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
+                      int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
+                      void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!X || !R || !Q || !valid_prec(prec) || m < 1 || n < 1 || n > 256 || ldx < m || ldq < m ||
+      ldr < n)
+    return RCQR_EINVAL;
+  if (perm && X == Q) return RCQR_EINVAL;
+  if (X == Q && elem_size(prec) != q_elem_size(prec)) return RCQR_EINVAL;
+  if (X == Q && ldx != ldq) return RCQR_EINVAL;
+  const size_t need = trsm_workspace(m, n, prec);
+  if (need > 0 && (!workspace || !aligned(workspace) || ws_bytes < need)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_trsm(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, w, stream));
+}
+
+rcqr_status rcqr_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
+                      const int64_t *rank, double *A, int64_t lda, void *workspace,
+                      size_t ws_bytes, cudaStream_t stream) {
+  if (!Q || !A || !valid_prec(prec) || m < 1 || n < 1 || n > 256 || ldq < m || lda < n)
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < gram_workspace(m, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  // Q's storage type: double for F64, float otherwise
+  const int qprec = prec == RCQR_F64 ? RCQR_F64 : RCQR_F32;
+  return cuda_status(launch_gram(Q, m, n, ldq, qprec, rank, A, lda, w, stream));
+}
+
+rcqr_status rcqr_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
+                             double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status,
+                             cudaStream_t stream) {
+  if (!A || !Rp || !R || n < 1 || n > 256 || lda < n || ldrp < n || ldr < n) return RCQR_EINVAL;
+  if (dev_status) {
+    rcqr_status s = cuda_status(launch_reset_status(dev_status, stream));
+    if (s != RCQR_OK) return s;
+  }
+  return cuda_status(launch_chol_update(A, n, lda, rank, Rp, ldrp, R, ldr, dev_status, stream));
+}
+
+rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                        uint64_t seed, int variant, double tau, void *Q, int64_t ldq, double *R,
+                        int64_t ldr, int32_t *perm, int64_t *rank, void *workspace,
+                        size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  if (!X || !Q || !R || !dev_status || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m ||
+      ldq < m || ldr < n || variant < 0 || variant > 3)
+    return RCQR_EINVAL;
+  const bool rr = variant == RCQR_RR || variant == RCQR_RR2;
+  const bool pass2 = variant == RCQR_DIRECT2 || variant == RCQR_RR2;
+  if (rr && (!perm || !(tau >= 0.0))) return RCQR_EINVAL;
+  if (X == Q && (rr || elem_size(prec) != q_elem_size(prec) || ldx != ldq)) return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < rcqr_workspace_size(m, n, k, variant, prec))
+    return RCQR_EWORKSPACE;
+
+  Workspace w(workspace, ws_bytes);
+  FactorBuffers b;
+  if (!take_factor_buffers(w, n, k, b)) return RCQR_EWORKSPACE;
+  const size_t mark = w.used;
+  auto scratch = [&]() {
+    w.used = mark;
+    return &w;
+  };
+  int64_t *rk = rank ? rank : b.rank_tmp;
+  const int qprec = prec == RCQR_F64 ? RCQR_F64 : RCQR_F32;
+
+#define RCQR_TRY(expr)                              \
+  do {                                              \
+    rcqr_status _s = cuda_status(expr);             \
+    if (_s != RCQR_OK) return _s;                   \
+  } while (0)
+
+  RCQR_TRY(launch_reset_status(dev_status, stream));
+  // Alg. 2 / Alg. 7 step 1 (with D of Sec. 4 in the same pass for RR)
+  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, rr ? b.colnorm2 : nullptr,
+                         *scratch(), stream));
+  const int32_t *pm = nullptr;
+  const int64_t *rkp = nullptr;
+  if (!rr) {
+    // Alg. 2 step 2
+    RCQR_TRY(launch_small_qr(b.P, k, n, k, nullptr, 0, R, ldr, *scratch(), stream));
+    RCQR_TRY(launch_set_rank(rk, n, stream));
+  } else {
+    // Alg. 7 steps 2-3 and the de-normalisation R <- R Pi^T D Pi
+    RCQR_TRY(launch_qrcp(b.P, k, n, k, b.colnorm2, tau, R, ldr, perm, rk, dev_status, *scratch(),
+                         stream));
+    pm = perm;
+    rkp = rk;
+  }
+  // Alg. 2 step 3 / Alg. 7 step 4: for RR the leading block of the
+  // de-normalised R is R11 D_sel, so Q = X Pi_{:,1:r} (R11 D_sel)^{-1}.
+  RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream));
+  if (pass2) {
+    // Alg. 3 steps 2-4 on the computed Q
+    RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
+    RCQR_TRY(launch_chol_update(b.A, n, n, rkp, b.Rp, n, R, ldr, dev_status, stream));
+    RCQR_TRY(launch_trsm(Q, m, n, ldq, qprec, b.Rp, n, nullptr, rkp, Q, ldq, *scratch(), stream));
+  }
+#undef RCQR_TRY
+  return RCQR_OK;
+}
+
+rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                         uint64_t seed, const double *L, int64_t l, int64_t ldl, double *Z,
+                         int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
+                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  if (!X || !Z || !R || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m || ldr < n ||
+      (S && lds < k))
+    return RCQR_EINVAL;
+  if (L == nullptr && l != k) return RCQR_EINVAL;
+  if (L != nullptr && (l < 1 || l > 2048 || ldl < l)) return RCQR_EINVAL;
+  if (ldz < l) return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < rcqr_workspace_size(m, n, k, 0, prec))
+    return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  FactorBuffers b;
+  if (!take_factor_buffers(w, n, k, b)) return RCQR_EWORKSPACE;
+  double *Y = nullptr;
+  if (L) {
+    Y = w.take<double>((size_t)l * n);
+    if (!Y) return RCQR_EWORKSPACE;
+  }
+  const size_t mark = w.used;
+  auto scratch = [&]() {
+    w.used = mark;
+    return &w;
+  };
+#define RCQR_TRY(expr)                              \
+  do {                                              \
+    rcqr_status _s = cuda_status(expr);             \
+    if (_s != RCQR_OK) return _s;                   \
+  } while (0)
+  if (dev_status) RCQR_TRY(launch_reset_status(dev_status, stream));
+  // Alg. 5 step 1
+  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, nullptr, *scratch(), stream));
+  if (L) RCQR_TRY(launch_dense_left(L, l, ldl, X, m, n, ldx, prec, Y, l, *scratch(), stream));
+  // Alg. 5 step 2
+  RCQR_TRY(launch_small_qr(b.P, k, n, k, S, lds, R, ldr, *scratch(), stream));
+  // Alg. 5 step 3: Z = Y R^{-1} (Y = P when L = Theta)
+  RCQR_TRY(launch_trsm(L ? Y : b.P, l, n, l == k && !L ? k : l, RCQR_F64, R, ldr, nullptr, nullptr,
+                       Z, ldz, *scratch(), stream));
+#undef RCQR_TRY
+  return RCQR_OK;
+}
+
+}  // extern "C"

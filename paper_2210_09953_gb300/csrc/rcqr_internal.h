@@ -1,0 +1,83 @@
+// Internal declarations shared by the translation units of librcqr.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/rcqr.h"
+
+namespace rcqr {
+
+// Theta levels packed for kernel arguments (256 signed 8-bit integers).
+struct ThetaTable {
+  int8_t level[256];
+};
+
+// Host-side table (own inverse-CDF code; identical integers to the definition
+// in rcqr.h) and the scale 1/sqrt(k v).
+const ThetaTable &theta_table();
+double theta_scale(int64_t k);
+
+// Bump allocator over the caller's workspace.  With base == nullptr it only
+// measures (used by rcqr_workspace_size), so sizes and layout agree.
+struct Workspace {
+  char *base;
+  size_t cap;
+  size_t used = 0;
+  Workspace(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+  template <class T>
+  T *take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + count * sizeof(T);
+    if (base == nullptr || used > cap) return nullptr;
+    return reinterpret_cast<T *>(base + off);
+  }
+  bool ok() const { return base != nullptr && used <= cap; }
+};
+
+int num_sms();
+
+inline size_t elem_size(int prec) { return prec == RCQR_F64 ? 8 : (prec == RCQR_F32 ? 4 : 2); }
+inline size_t q_elem_size(int prec) { return prec == RCQR_F64 ? 8 : 4; }
+
+// ---- sketch (P = Theta X), FP64-exact accumulation --------------------------
+// Number of per-CTA partial sketches the sketch kernel writes (workspace sizing).
+int sketch_groups(int64_t m, int64_t n, int64_t k, int64_t row_offset);
+size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec);
+cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                          uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
+                          int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st);
+// Dense Y = L X (l x n double), L an explicit l x m double matrix.
+cudaError_t launch_dense_left(const double *L, int64_t l, int64_t ldl, const void *X, int64_t m,
+                              int64_t n, int64_t ldx, int prec, double *Y, int64_t ldy,
+                              Workspace &ws, cudaStream_t st);
+size_t dense_left_workspace(int64_t l, int64_t m, int64_t n);
+
+// ---- small dense FP64 kernels (one CTA each) --------------------------------
+size_t small_qr_workspace(int64_t k, int64_t n);
+cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, double *S,
+                            int64_t lds, double *R, int64_t ldr, Workspace &ws, cudaStream_t st);
+cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
+                        double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                        int *dev_status, Workspace &ws, cudaStream_t st);
+cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
+                               double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status,
+                               cudaStream_t st);
+// W = R^{-1} (n x n upper) for the leading rank x rank block (rank nullable).
+cudaError_t launch_tri_inverse(const double *R, int64_t n, int64_t ldr, const int64_t *rank,
+                               double *W, int64_t ldw, cudaStream_t st);
+cudaError_t launch_reset_status(int *dev_status, cudaStream_t st);
+cudaError_t launch_set_rank(int64_t *rank, int64_t value, cudaStream_t st);
+
+// ---- bulk kernels over m -----------------------------------------------------
+size_t trsm_workspace(int64_t m, int64_t n, int prec);
+cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                        const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
+                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st);
+size_t gram_workspace(int64_t m, int64_t n);
+cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
+                        const int64_t *rank, double *A, int64_t lda, Workspace &ws,
+                        cudaStream_t st);
+
+}  // namespace rcqr
