@@ -221,6 +221,9 @@ def test_factor_direct_parity(rc, inputs, prec, variant, m, n, k, cond):
     kap = orc.condition_number(Xh)
     uq = U if prec == "f64" else 2.0 ** -24
     tol_r = max(1e-12, 10 * n * U * kap)
+    if variant == 1 and prec != "f64":
+        # pass 2 works on Q rounded to float: R' = chol(fl32(Q)^T fl32(Q)) moves by O(sqrt(n) u32)
+        tol_r += 10 * math.sqrt(n) * uq
     assert colrel(Rg, Ro) <= tol_r
     assert np.linalg.norm(Qg @ Rg - Qo @ Ro) / np.linalg.norm(Xh) <= max(1e-12, 10 * uq)
     if variant == 1:
