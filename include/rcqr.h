@@ -91,6 +91,24 @@ rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         double *P, int64_t ldp, double *colnorm2,
                         void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+/* rcqr_sketch without a workspace argument, for callers that cannot provide
+ * device scratch memory: a plugin whose fixed argument list has no room for a
+ * workspace pointer, or code inside a host application that owns all device
+ * memory through its own pool and forbids further allocations.  The paper has
+ * no counterpart; it is a packaging choice of this library.
+ * Same inputs and outputs as rcqr_sketch (row_offset included).  The partial
+ * sums live in one 8 MiB array in the library's own device memory, which every
+ * GPU that loads the library keeps until the process exits; this call never
+ * allocates or frees memory.  The first call on each device looks the array's
+ * address up, so make it before any stream capture on that device.  All calls
+ * share the array: calls whose GPU work overlaps (streams not ordered with
+ * each other) race on it.  Returns RCQR_EWORKSPACE when n*k (+ 2 x SM count x n
+ * with colnorm2) exceeds the 2^20 doubles of the array, RCQR_EINVAL on bad
+ * arguments. */
+rcqr_status rcqr_sketch_noalloc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                                int64_t k, uint64_t seed, int64_t row_offset,
+                                double *P, int64_t ldp, double *colnorm2, cudaStream_t stream);
+
 /* Householder QR of a small k x n double matrix (Alg. 2 step 2, Sec. 3.1):
  * P = S R with S (k x n, orthonormal columns, nullable) and R (n x n, upper,
  * diag(R) >= 0, strictly lower part set to 0). */

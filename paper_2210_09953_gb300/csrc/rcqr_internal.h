@@ -48,6 +48,12 @@ size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int
 cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                           uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                           int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st);
+// The same sketch with its partial sums in a caller-given device buffer of
+// scratch_doubles doubles (fewer row groups when the buffer is small); no workspace.
+cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                               int64_t k, uint64_t seed, int64_t row_offset, double *P,
+                               int64_t ldp, double *colnorm2, double *scratch,
+                               size_t scratch_doubles, cudaStream_t st);
 // Dense Y = L X (l x n double), L an explicit l x m double matrix.
 cudaError_t launch_dense_left(const double *L, int64_t l, int64_t ldl, const void *X, int64_t m,
                               int64_t n, int64_t ldx, int prec, double *Y, int64_t ldy,

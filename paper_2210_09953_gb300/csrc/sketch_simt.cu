@@ -273,6 +273,57 @@ cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                               int64_t k, uint64_t seed, int64_t row_offset, double *P,
+                               int64_t ldp, double *colnorm2, double *scratch,
+                               size_t scratch_doubles, cudaStream_t st) {
+  int64_t tile0, ntiles;
+  tile_range(m, row_offset, &tile0, &ntiles);
+  const int64_t chunks = ((k + kChunkK - 1) / kChunkK) * ((n + kChunkN - 1) / kChunkN);
+  int64_t groups = choose_groups(ntiles, chunks);
+  const int cg = colnorm2 ? colnorm_groups(m) : 0;
+  const int64_t room = (int64_t)scratch_doubles - (int64_t)cg * n;
+  groups = std::min<int64_t>(groups, room / (n * k));
+  if (groups < 1) return cudaErrorInvalidValue;
+  double *partial = scratch;
+  double *cp = scratch + groups * n * k;
+  dim3 grid((unsigned)chunks, (unsigned)groups);
+  const ThetaTable &tab = theta_table();
+  switch (prec) {
+    case RCQR_F64:
+      sketch_partial_kernel<double><<<grid, kThreads, 0, st>>>(
+          (const double *)X, m, (int)n, ldx, (int)k, seed, 0, row_offset, tile0, ntiles,
+          (int)groups, tab, partial);
+      break;
+    case RCQR_F32:
+      sketch_partial_kernel<float><<<grid, kThreads, 0, st>>>(
+          (const float *)X, m, (int)n, ldx, (int)k, seed, 0, row_offset, tile0, ntiles,
+          (int)groups, tab, partial);
+      break;
+    default:
+      sketch_partial_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(
+          (const __nv_bfloat16 *)X, m, (int)n, ldx, (int)k, seed, 0, row_offset, tile0, ntiles,
+          (int)groups, tab, partial);
+  }
+  sketch_reduce_kernel<<<(unsigned)((k * n + 255) / 256), 256, 0, st>>>(
+      partial, (int)groups, (int)k, (int)n, theta_scale(k), P, ldp);
+  if (colnorm2) {
+    switch (prec) {
+      case RCQR_F64:
+        colnorm_partial_kernel<double><<<cg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, cg, cp);
+        break;
+      case RCQR_F32:
+        colnorm_partial_kernel<float><<<cg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, cg, cp);
+        break;
+      default:
+        colnorm_partial_kernel<__nv_bfloat16><<<cg, 256, 0, st>>>((const __nv_bfloat16 *)X, m,
+                                                                  (int)n, ldx, cg, cp);
+    }
+    colnorm_reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cp, cg, (int)n, colnorm2);
+  }
+  return cudaGetLastError();
+}
+
 size_t dense_left_workspace(int64_t l, int64_t m, int64_t n) {
   const int64_t chunks = ((l + kChunkK - 1) / kChunkK) * ((n + kChunkN - 1) / kChunkN);
   const int groups = choose_groups((m + kLRows - 1) / kLRows, chunks);
