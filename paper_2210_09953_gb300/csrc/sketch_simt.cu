@@ -1,4 +1,7 @@
-// Sketch P = Theta X (Alg. 2 step 1) on CUDA cores with FP64 accumulation.
+// Sketch P = Theta X (Alg. 2 step 1) on CUDA cores with FP64 accumulation (the
+// kernel behind rcqr_sketch_noalloc), the squared column norms, the dense left
+// product Y = L X of the reduced variant, and the entry of the factorization
+// path's sketch, which runs the exact tensor-core kernel of sketch_tc.cu.
 //
 // Split-K over the long dimension m: CTA (chunk, g) walks a contiguous range
 // of 64-row tiles of X (tiles aligned to multiples of 64 in *global* row
@@ -216,61 +219,43 @@ int sketch_groups(int64_t m, int64_t n, int64_t k, int64_t row_offset) {
 }
 
 size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
-  (void)prec;
   Workspace w(nullptr, 0);
-  w.take<double>((size_t)sketch_groups(m, n, k, row_offset) * n * k);
+  w.take<char>(sketch_tc_workspace(m, n, k, row_offset, prec));
   w.take<double>((size_t)colnorm_groups(m) * n);
   return w.used;
 }
 
-cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
-                          uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
-                          int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st) {
-  int64_t tile0, ntiles;
-  tile_range(m, row_offset, &tile0, &ntiles);
-  const int64_t chunks = ((k + kChunkK - 1) / kChunkK) * ((n + kChunkN - 1) / kChunkN);
-  const int groups = choose_groups(ntiles, chunks);
-  double *partial = ws.take<double>((size_t)groups * n * k);
-  if (!partial) return cudaErrorMemoryAllocation;
-  dim3 grid((unsigned)chunks, (unsigned)groups);
-  const ThetaTable &tab = theta_table();
+cudaError_t launch_colnorm2(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, double *out,
+                            Workspace &ws, cudaStream_t st) {
+  const int cg = colnorm_groups(m);
+  double *cp = ws.take<double>((size_t)cg * n);
+  if (!cp) return cudaErrorMemoryAllocation;
   switch (prec) {
     case RCQR_F64:
-      sketch_partial_kernel<double><<<grid, kThreads, 0, st>>>(
-          (const double *)X, m, (int)n, ldx, (int)k, seed, stream_id, row_offset, tile0, ntiles,
-          groups, tab, partial);
+      colnorm_partial_kernel<double><<<cg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, cg, cp);
       break;
     case RCQR_F32:
-      sketch_partial_kernel<float><<<grid, kThreads, 0, st>>>(
-          (const float *)X, m, (int)n, ldx, (int)k, seed, stream_id, row_offset, tile0, ntiles,
-          groups, tab, partial);
+      colnorm_partial_kernel<float><<<cg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, cg, cp);
       break;
     default:
-      sketch_partial_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(
-          (const __nv_bfloat16 *)X, m, (int)n, ldx, (int)k, seed, stream_id, row_offset, tile0,
-          ntiles, groups, tab, partial);
+      colnorm_partial_kernel<__nv_bfloat16><<<cg, 256, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n,
+                                                                ldx, cg, cp);
   }
-  const int64_t total = k * n;
-  sketch_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-      partial, groups, (int)k, (int)n, theta_scale(k), P, ldp);
-  if (colnorm2) {
-    const int cg = colnorm_groups(m);
-    double *cp = ws.take<double>((size_t)cg * n);
-    if (!cp) return cudaErrorMemoryAllocation;
-    switch (prec) {
-      case RCQR_F64:
-        colnorm_partial_kernel<double><<<cg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, cg, cp);
-        break;
-      case RCQR_F32:
-        colnorm_partial_kernel<float><<<cg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, cg, cp);
-        break;
-      default:
-        colnorm_partial_kernel<__nv_bfloat16><<<cg, 256, 0, st>>>((const __nv_bfloat16 *)X, m,
-                                                                  (int)n, ldx, cg, cp);
-    }
-    colnorm_reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cp, cg, (int)n, colnorm2);
-  }
+  colnorm_reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cp, cg, (int)n, out);
   return cudaGetLastError();
+}
+
+// The sketch of the factorization path: the exact tensor-core kernel
+// (sketch_tc.cu) plus, for the rank-revealing variant, the column norms.
+cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                          uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
+                          int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st,
+                          int *dev_status) {
+  cudaError_t e = launch_sketch_tc(X, m, n, ldx, prec, k, seed, stream_id, row_offset, P, ldp,
+                                   dev_status, ws, st);
+  if (e != cudaSuccess) return e;
+  if (colnorm2) return launch_colnorm2(X, m, n, ldx, prec, colnorm2, ws, st);
+  return cudaSuccess;
 }
 
 cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,

@@ -1,8 +1,12 @@
 """GPU parity: every stage of the CUDA path against the CPU FP64 oracle on the same seeded inputs.
 
 Tolerances (stated per result; u = 2^-53):
-* sketch P: column-wise relative 1e-12 (FP64 sums in a different order);
-  integer X: bit-exact.
+* sketch P, column-wise relative (SKETCH_TOL): FP64 X 1e-12; FP32 X 1e-11
+  (the tensor-core sketch keeps 3 exact 7-bit slices and rounds the last two
+  in one fp32 accumulator, ~2^-39 of each 1024-row block's largest |x|);
+  BF16 X 1e-6 (3 slices: 21 bits below the block's largest |x|).  All three
+  are far below Assumptions 5.1's 0.1 u n^{-1/2} for the storage precision.
+  Integer X: bit-exact.
 * small QR / QRCP / Cholesky: R, S relative to column norms <= max(1e-12, 10 n u cond).
 * forward substitution: Q column-relative <= max(1e-12, 10 n u cond(R)) in FP64;
   FP32 output: additionally 2^-23 (one rounding to float).
@@ -20,6 +24,7 @@ from oracle import rcqr as orc
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
+SKETCH_TOL = {"f64": 1e-12, "f32": 1e-11, "bf16": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +70,7 @@ def test_sketch_parity(rc, inputs, prec, m, n, k, off):
     torch.cuda.synchronize()
     Xh = host64(X)
     Po = orc.sketch(Xh, k, 0xABC + n, row_offset=off)
-    assert colrel(host64(P), Po) <= 1e-12
+    assert colrel(host64(P), Po) <= SKETCH_TOL[prec]
     assert np.max(np.abs(host64(cn) - np.sum(Xh * Xh, axis=0)) / np.sum(Xh * Xh, axis=0)) <= 1e-13
 
 
@@ -92,7 +97,7 @@ def test_sketch_ld_larger_than_m(rc, inputs):
     X = inputs.svd_matrix(1000, 9, 1e2, 8, dtype="f32", device=DEV, ld=1024)
     assert X.stride() == (1, 1024)
     P = rc.rcqr_sketch(X, 32, 7)
-    assert colrel(host64(P), orc.sketch(host64(X), 32, 7)) <= 1e-12
+    assert colrel(host64(P), orc.sketch(host64(X), 32, 7)) <= SKETCH_TOL["f32"]
 
 
 # ----------------------------------------------------------------------------- small kernels
@@ -220,7 +225,8 @@ def test_factor_direct_parity(rc, inputs, prec, variant, m, n, k, cond):
     # stored X's condition number (rounding to f32/bf16 changes it)
     kap = orc.condition_number(Xh)
     uq = U if prec == "f64" else 2.0 ** -24
-    tol_r = max(1e-12, 10 * n * U * kap)
+    # forward errors of R (and of Q before pass 2) move by ~cond x the sketch's relative error
+    tol_r = max(1e-12, 10 * n * U * kap) + 10 * math.sqrt(n) * kap * (0 if prec == "f64" else SKETCH_TOL[prec])
     if variant == 1 and prec != "f64":
         # pass 2 works on Q rounded to float: R' = chol(fl32(Q)^T fl32(Q)) moves by O(sqrt(n) u32)
         tol_r += 10 * math.sqrt(n) * uq
@@ -229,7 +235,7 @@ def test_factor_direct_parity(rc, inputs, prec, variant, m, n, k, cond):
     if variant == 1:
         assert orc.orthogonality(Qg) <= max(1e-12, 100 * n * uq)
     else:
-        assert colrel(Qg, Qo) <= max(1e-12, 10 * n * U * kap) + (0 if prec == "f64" else 2.0 ** -23)
+        assert colrel(Qg, Qo) <= tol_r + (0 if prec == "f64" else 2.0 ** -23)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

@@ -5,7 +5,7 @@ that owns all device memory through its own pool) cannot hand the library a
 workspace.  This entry point keeps its partial sums in the library's own
 fixed device array instead.  The test calls it through the C ABI twice in a
 row, on two different shapes, and checks each result against rcqr_sketch
-(same column-wise tolerance as the other sketch tests) and that the calls
+(the column-wise tolerance the sketch parity tests state for each precision) and that the calls
 after the first change no device memory usage.  This file is collected last
 so that a failure here does not hide the other tests' results.
 """
@@ -16,6 +16,8 @@ import pytest
 import torch
 
 pytestmark = pytest.mark.gpu
+# the column-wise sketch tolerances the parity tests state (FP64 X / FP32 X)
+SKETCH_TOL = {"f64": 1e-12, "f32": 1e-11}
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +67,7 @@ def test_noalloc_sketch_matches_workspace_sketch_twice(rc):
         cn_ref = torch.empty(n, dtype=torch.float64, device="cuda")
         P_ref = rc.rcqr_sketch(X, k, 0xFEED + n, row_offset=off, colnorm2=cn_ref)
         torch.cuda.synchronize()
-        assert _colrel(P, P_ref) <= 1e-12
+        assert _colrel(P, P_ref) <= SKETCH_TOL[dt]
         assert float(torch.max(torch.abs(cn - cn_ref) / cn_ref)) <= 1e-13
         del X, P, cn, P_ref, cn_ref
     torch.cuda.synchronize()
