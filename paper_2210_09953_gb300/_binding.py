@@ -148,13 +148,16 @@ def rcqr_qrcp(P, tau, colnorm2=None):
     return R, perm, rank, status
 
 
-def rcqr_trsm(X, R, perm=None, rank=None, Q=None):
+def rcqr_trsm(X, R, perm=None, rank=None, Q=None, workspace=None):
     m, n = X.shape
     prec = prec_of(X.dtype)
     if Q is None:
         Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, X.device)
+    ws = workspace if workspace is not None else _workspace(
+        rcqr_workspace_size(m, n, max(8, (n + 7) // 8 * 8), DIRECT, prec), X.device)
+    wp, wb = _aligned_ptr(ws)
     _check("rcqr_trsm", lib.rcqr_trsm(_ptr(X), m, n, _ld(X), prec, _ptr(R), _ld(R), _ptr(perm), _ptr(rank),
-                                      _ptr(Q), _ld(Q), None, 0, _stream()))
+                                      _ptr(Q), _ld(Q), wp, wb, _stream()))
     return Q
 
 

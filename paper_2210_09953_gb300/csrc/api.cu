@@ -216,7 +216,7 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   RCQR_TRY(launch_reset_status(dev_status, stream));
   // Alg. 2 / Alg. 7 step 1 (with D of Sec. 4 in the same pass for RR)
   RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, rr ? b.colnorm2 : nullptr,
-                         *scratch(), stream));
+                         *scratch(), stream, dev_status));
   const int32_t *pm = nullptr;
   const int64_t *rkp = nullptr;
   if (!rr) {
@@ -232,12 +232,13 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   }
   // Alg. 2 step 3 / Alg. 7 step 4: for RR the leading block of the
   // de-normalised R is R11 D_sel, so Q = X Pi_{:,1:r} (R11 D_sel)^{-1}.
-  RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream));
+  RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream, dev_status));
   if (pass2) {
     // Alg. 3 steps 2-4 on the computed Q
     RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
     RCQR_TRY(launch_chol_update(b.A, n, n, rkp, b.Rp, n, R, ldr, dev_status, stream));
-    RCQR_TRY(launch_trsm(Q, m, n, ldq, qprec, b.Rp, n, nullptr, rkp, Q, ldq, *scratch(), stream));
+    RCQR_TRY(launch_trsm(Q, m, n, ldq, qprec, b.Rp, n, nullptr, rkp, Q, ldq, *scratch(), stream,
+                         dev_status));
   }
 #undef RCQR_TRY
   return RCQR_OK;

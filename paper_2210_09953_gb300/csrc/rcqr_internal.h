@@ -89,7 +89,17 @@ cudaError_t launch_set_rank(int64_t *rank, int64_t value, cudaStream_t st);
 size_t trsm_workspace(int64_t m, int64_t n, int prec);
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
-                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st);
+                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st,
+                        int *dev_status = nullptr);
+// FP32 substitution and Gram of the mixed path (trsm_f32.cu).
+bool trsm32_supported(int64_t n);
+size_t trsm32_workspace(int64_t n);
+cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
+                          int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
+                          Workspace &ws, cudaStream_t st);
+int gram32_groups(int64_t m, int64_t n);
+cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
+                          double *partial, int groups, cudaStream_t st);
 size_t gram_workspace(int64_t m, int64_t n);
 cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
                         const int64_t *rank, double *A, int64_t lda, Workspace &ws,

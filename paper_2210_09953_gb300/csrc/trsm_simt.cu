@@ -1,5 +1,6 @@
 // Forward substitution Q = X R^{-1} (Alg. 2 step 3) and the Gram matrix
-// A = Q^T Q (Alg. 3 step 2) on CUDA cores in FP64.
+// A = Q^T Q (Alg. 3 step 2) on CUDA cores in FP64 (the FP64 path), and the
+// dispatch to the FP32 kernels of the mixed path (trsm_f32.cu).
 //
 // Substitution: the rows of X are independent (the property Sec. 5.1 uses to
 // sketch the rounding errors row by row), so one thread owns one row and runs
@@ -129,15 +130,17 @@ int gram_groups(int64_t m, int64_t n) {
 
 size_t trsm_workspace(int64_t m, int64_t n, int prec) {
   (void)m;
-  (void)n;
-  (void)prec;
-  return 0;
+  return (prec != RCQR_F64 && trsm32_supported(n)) ? trsm32_workspace(n) : 0;
 }
 
+// FP64 X: row-wise substitution in FP64 (here).  FP32 / BF16 X (n <= 128): the
+// FP32 substitution of trsm_f32.cu, the working precision of the mixed path.
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
-                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st) {
-  (void)ws;
+                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st, int *dev_status) {
+  (void)dev_status;
+  if (prec != RCQR_F64 && trsm32_supported(n))
+    return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st);
   const unsigned blocks = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
   switch (prec) {
     case RCQR_F64:
@@ -157,13 +160,22 @@ cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
 
 size_t gram_workspace(int64_t m, int64_t n) {
   Workspace w(nullptr, 0);
-  w.take<double>((size_t)gram_groups(m, n) * n * n);
+  w.take<double>((size_t)std::max(gram_groups(m, n), gram32_groups(m, n)) * n * n);
   return w.used;
 }
 
 cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
                         const int64_t *rank, double *A, int64_t lda, Workspace &ws,
                         cudaStream_t st) {
+  if (prec != RCQR_F64) {
+    const int g32 = gram32_groups(m, n);
+    double *p32 = ws.take<double>((size_t)g32 * n * n);
+    if (!p32) return cudaErrorMemoryAllocation;
+    cudaError_t e = launch_gram32((const float *)Q, m, n, ldq, rank, p32, g32, st);
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(p32, g32, (int)n, A, lda);
+    return cudaGetLastError();
+  }
   const int groups = gram_groups(m, n);
   double *partial = ws.take<double>((size_t)groups * n * n);
   if (!partial) return cudaErrorMemoryAllocation;

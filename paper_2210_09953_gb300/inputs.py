@@ -40,10 +40,26 @@ def _gen(seed, device):
 
 
 def orthonormal(m, n, seed, device="cpu"):
-    """Q factor (m x n) of a seeded standard Gaussian matrix, FP64."""
+    """Orthonormal m x n matrix from a seeded standard Gaussian, FP64.
+
+    Small or square matrices: the Q factor of LAPACK's QR on the host.  Tall
+    ones (m > 8192, m >= 4n): the orthogonal polar factor of G / sqrt(m) by
+    Newton-Schulz iterations U <- U (3 I - U^T U) / 2, plain matrix products on
+    the device (the singular values of G / sqrt(m) lie in 1 +- ~sqrt(n/m), well
+    inside the iteration's convergence region (0, sqrt 3)).
+    """
     G = torch.randn((m, n), dtype=torch.float64, device=device, generator=_gen(seed, device))
-    Q, _ = torch.linalg.qr(G, mode="reduced")
-    return Q
+    if m <= 8192 or m < 4 * n:
+        Q, _ = torch.linalg.qr(G.cpu(), mode="reduced")
+        return Q.to(device)
+    U = G / (m ** 0.5)
+    eye = torch.eye(n, dtype=torch.float64, device=device)
+    for _ in range(40):
+        A = U.t() @ U
+        if float(torch.max(torch.abs(A - eye))) < 1e-15:
+            break
+        U = U @ (1.5 * eye - 0.5 * A)
+    return U
 
 
 def svd_matrix(m, n, cond, seed, dtype="f64", device="cpu", ld=None, return_factors=False):

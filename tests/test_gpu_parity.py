@@ -175,9 +175,19 @@ def test_trsm_parity(rc, inputs, prec, m, n, cond):
     R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
     Q = rc.rcqr_trsm(X, R)
     torch.cuda.synchronize()
-    Qo = olin.forward_substitution(host64(X), Ro)
-    tol = max(1e-12, 10 * n * U * cond) + (0 if prec == "f64" else 2.0 ** -23)
-    assert colrel(host64(Q), Qo) <= tol
+    Xh = host64(X)
+    Qo = olin.forward_substitution(Xh, Ro)
+    Qg = host64(Q)
+    if prec == "f64":
+        assert colrel(Qg, Qo) <= max(1e-12, 10 * n * U * cond)
+    else:
+        # FP32 substitution (the mixed path's working precision u = 2^-24): row-wise
+        # backward error |X - Q R| <= (n + 3) u |Q||R| (Higham Thm 8.5, plus R and Q
+        # rounded to float), hence a forward error <= (n + 3) u cond(R) column-wise.
+        u32 = 2.0 ** -24
+        E = np.abs(Xh - Qg @ Ro)
+        assert np.all(E <= 2 * (n + 3) * u32 * (np.abs(Qg) @ np.abs(Ro)) + 1e-300)
+        assert colrel(Qg, Qo) <= 2 * (n + 3) * u32 * cond + 2 * u32
 
 
 def test_trsm_permuted_rank(rc, inputs):
@@ -202,7 +212,13 @@ def test_gram_parity(rc, inputs, prec, m, n):
     torch.cuda.synchronize()
     Qh = host64(Q)
     Ao = Qh.T @ Qh
-    assert np.max(np.abs(host64(A) - Ao)) <= 1e-13 * np.max(np.abs(Ao))
+    if prec == "f64":
+        assert np.max(np.abs(host64(A) - Ao)) <= 1e-13 * np.max(np.abs(Ao))
+    else:
+        # FP32 products summed in FP32 over 64-row chunks (<= 66 roundings each), the chunk
+        # sums compensated: |dA| <= 66 u32 (|Q|^T |Q|) entrywise
+        scale = np.abs(Qh).T @ np.abs(Qh)
+        assert np.all(np.abs(host64(A) - Ao) <= 66 * 2.0 ** -24 * scale)
 
 
 # ----------------------------------------------------------------------------- end to end
@@ -224,18 +240,22 @@ def test_factor_direct_parity(rc, inputs, prec, variant, m, n, k, cond):
     Qg, Rg = host64(Q), host64(R)
     # stored X's condition number (rounding to f32/bf16 changes it)
     kap = orc.condition_number(Xh)
-    uq = U if prec == "f64" else 2.0 ** -24
-    # forward errors of R (and of Q before pass 2) move by ~cond x the sketch's relative error
+    ub = U if prec == "f64" else 2.0 ** -24          # unit roundoff of the bulk steps
+    # backward error: X = Q R up to the bulk precision, at every condition number (Thm 5.2 (main1))
+    assert np.linalg.norm(Qg @ Rg - Xh) / np.linalg.norm(Xh) <= max(1e-12, 10 * n * ub)
+    if variant == 1 and prec == "f64":
+        assert orc.orthogonality(Qg) <= max(1e-12, 100 * n * ub)
+    # forward errors: R comes from the sketch (FP64-level) in pass 1; in pass 2 and in Q the
+    # bulk precision enters amplified by cond -- checked where that product is small
     tol_r = max(1e-12, 10 * n * U * kap) + 10 * math.sqrt(n) * kap * (0 if prec == "f64" else SKETCH_TOL[prec])
     if variant == 1 and prec != "f64":
-        # pass 2 works on Q rounded to float: R' = chol(fl32(Q)^T fl32(Q)) moves by O(sqrt(n) u32)
-        tol_r += 10 * math.sqrt(n) * uq
-    assert colrel(Rg, Ro) <= tol_r
-    assert np.linalg.norm(Qg @ Rg - Qo @ Ro) / np.linalg.norm(Xh) <= max(1e-12, 10 * uq)
-    if variant == 1:
-        assert orc.orthogonality(Qg) <= max(1e-12, 100 * n * uq)
-    else:
-        assert colrel(Qg, Qo) <= tol_r + (0 if prec == "f64" else 2.0 ** -23)
+        tol_r += 10 * n * ub * kap
+    if tol_r < 1e-2:
+        assert colrel(Rg, Ro) <= tol_r
+        if variant == 0:
+            assert colrel(Qg, Qo) <= tol_r + 10 * n * ub * kap + 2 * ub
+        elif prec != "f64":
+            assert orc.orthogonality(Qg) <= 100 * n * ub
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
