@@ -125,7 +125,9 @@ rcqr_status rcqr_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, do
     return RCQR_EINVAL;
   if (!workspace || !aligned(workspace) || ws_bytes < small_qr_workspace(k, n)) return RCQR_EWORKSPACE;
   Workspace w(workspace, ws_bytes);
-  return cuda_status(launch_small_qr(P, k, n, ldp, S, lds, R, ldr, w, stream));
+  // S wanted: one CTA forms the reflectors and S; R only: the TSQR tree
+  if (S) return cuda_status(launch_small_qr(P, k, n, ldp, S, lds, R, ldr, w, stream));
+  return cuda_status(launch_small_r(P, k, n, ldp, R, ldr, w, stream));
 }
 
 rcqr_status rcqr_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
@@ -221,7 +223,7 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   const int64_t *rkp = nullptr;
   if (!rr) {
     // Alg. 2 step 2
-    RCQR_TRY(launch_small_qr(b.P, k, n, k, nullptr, 0, R, ldr, *scratch(), stream));
+    RCQR_TRY(launch_small_r(b.P, k, n, k, R, ldr, *scratch(), stream));
     RCQR_TRY(launch_set_rank(rk, n, stream));
   } else {
     // Alg. 7 steps 2-3 and the de-normalisation R <- R Pi^T D Pi

@@ -30,4 +30,15 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return t;
 }
 
+// sum_{g < G} src[g * stride] by one warp in a fixed order (lane l adds g = l, l+32, ...
+// in increasing order, then a fixed shuffle-down tree); the total is returned in lane 0.
+__device__ __forceinline__ double warp_sum_strided(const double *src, int G, int64_t stride) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int g = lane; g < G; g += 32) s += src[(int64_t)g * stride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
 }  // namespace rcqr

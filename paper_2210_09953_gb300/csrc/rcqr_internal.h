@@ -73,6 +73,9 @@ size_t dense_left_workspace(int64_t l, int64_t m, int64_t n);
 size_t small_qr_workspace(int64_t k, int64_t n);
 cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, double *S,
                             int64_t lds, double *R, int64_t ldr, Workspace &ws, cudaStream_t st);
+// R only (diag >= 0) by a TSQR tree over several CTAs.
+cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, double *R, int64_t ldr,
+                           Workspace &ws, cudaStream_t st);
 cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
                         double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         int *dev_status, Workspace &ws, cudaStream_t st);

@@ -424,14 +424,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   if (warp == 0) umma::tmem_dealloc(tbase, NCOLS);
 }
 
+// P(i, j) = c * sum_g partial[g](i, j): one warp per entry, fixed order.
 __global__ void sketch_tc_reduce_kernel(const double *__restrict__ partial, int groups, int k, int n,
                                         double c, double *__restrict__ P, int64_t ldp) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (idx >= (int64_t)k * n) return;
   const int i = (int)(idx % k), j = (int)(idx / k);
-  double s = 0.0;
-  for (int g = 0; g < groups; ++g) s += partial[((int64_t)g * n + j) * k + i];
-  P[i + (int64_t)j * ldp] = c * s;
+  const double s = warp_sum_strided(partial + (int64_t)j * k + i, groups, (int64_t)n * k);
+  if ((threadIdx.x & 31) == 0) P[i + (int64_t)j * ldp] = c * s;
 }
 
 struct TcPlan {
@@ -547,7 +547,7 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
     default: e = launch_tc_prec<RCQR_BF16>(a, p, grid, st);
   }
   if (e != cudaSuccess) return e;
-  sketch_tc_reduce_kernel<<<(unsigned)((k * n + 255) / 256), 256, 0, st>>>(partial, p.groups, (int)k, (int)n,
+  sketch_tc_reduce_kernel<<<(unsigned)((k * n * 32 + 255) / 256), 256, 0, st>>>(partial, p.groups, (int)k, (int)n,
                                                                           theta_scale(k), P, ldp);
   return cudaGetLastError();
 }

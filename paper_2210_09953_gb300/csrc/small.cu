@@ -1,13 +1,20 @@
-// Small dense FP64 kernels of the method (one CTA each; the matrices are at
-// most 2048 x 256):
+// Small dense FP64 kernels of the method (the matrices are at most 2048 x 256):
 //  * Householder QR of the sketch P (Alg. 2 step 2; the paper's choice of
-//    reflections, Sec. 3.1), diag(R) >= 0, S formed explicitly;
+//    reflections, Sec. 3.1), diag(R) >= 0, S formed explicitly when asked;
+//  * R alone by a tree over several CTAs (TSQR: leaf Householder QRs, then
+//    folds of stacked triangles);
 //  * column-pivoted Householder QR of P D^{-1}, the truncation rank and the
 //    de-normalisation R <- R Pi^T D Pi (Alg. 7 steps 2, 3, 5 and Sec. 4);
 //  * Cholesky of the Gram matrix with R <- R' R (Alg. 3 step 3);
 //  * the inverse of an upper triangular matrix.
-// The working copy of P lives in shared memory when it fits, else in the
-// caller's workspace (L2 resident: at most 4 MB).
+//
+// GB300 issues FP64 at a few flops per clock per SM, so these kernels keep the
+// FP64 instruction count minimal: one thread owns one column's dot product and
+// update (no per-column shuffle reductions), the scalars of a reflector or a
+// pivot are computed once and broadcast through shared memory, and the working
+// copy has an odd leading dimension so that column-per-lane access is
+// conflict-free.  The working copy lives in shared memory when it fits, else in
+// the caller's workspace (L2 resident).
 #include <algorithm>
 
 #include "common.cuh"
@@ -17,92 +24,118 @@ namespace rcqr {
 
 namespace {
 
-constexpr int kSmallThreads = 512;
+constexpr int kSmallThreads = 256;
 constexpr size_t kSmemLimit = 200 * 1024;
 
-// One Householder step on column j of the k x n matrix A (column-major, lda):
-// builds v in A[j:, j] (A[j,j] <- v0), returns via shared d/beta, and applies
-// the reflector to columns j+1 .. n-1.
-__device__ void householder_step(double *A, int k, int n, int64_t lda, int j, double *red,
-                                 double *s_beta, double *s_diag) {
+__device__ __forceinline__ int odd_ld(int rows) { return rows | 1; }
+
+// Sum over lane-strided terms of warp 0 (call from warp 0 only): lane 0 gets the total.
+__device__ __forceinline__ double warp0_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Dot products for the column updates: four threads per column, each summing
+// every fourth row with two accumulators, the quarter sums combined by two
+// shuffles (fixed order).  Returns the full sum in all four threads.
+__device__ __forceinline__ double quad_dot(const double *a, const double *b, int i0, int i1, int q) {
+  double s0 = 0.0, s1 = 0.0;
+  int i = i0 + q;
+  for (; i + 4 < i1; i += 8) {
+    s0 = fma(a[i], b[i], s0);
+    s1 = fma(a[i + 4], b[i + 4], s1);
+  }
+  if (i < i1) s0 = fma(a[i], b[i], s0);
+  double s = s0 + s1;
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+// One Householder step on column j of the rows x n matrix A (column-major, lda):
+// v is built in A[j:, j] (A[j, j] <- v0); s_beta[j], s_diag[j] receive beta and
+// the new diagonal entry; columns j+1.. are updated, one thread per column.
+__device__ void householder_step(double *A, int rows, int n, int lda, int j, double *s_beta,
+                                 double *s_diag) {
   double *col = A + (int64_t)j * lda;
-  double tail = 0.0;
-  for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) tail = fma(col[i], col[i], tail);
-  tail = block_sum(tail, red);
-  const double x0 = col[j];
-  const double sigma = fma(x0, x0, tail);
-  double beta = 0.0, d = 0.0;
-  if (sigma > 0.0) {
-    const double alpha = sqrt(sigma);
-    const double s = x0 >= 0.0 ? 1.0 : -1.0;
-    const double v0 = x0 + s * alpha;
-    beta = 2.0 / fma(v0, v0, tail);
-    d = -s * alpha;
-    __syncthreads();
-    if (threadIdx.x == 0) col[j] = v0;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < rows; i += 32) t = fma(col[i], col[i], t);
+    t = warp0_sum(t);
+    if (threadIdx.x == 0) {
+      const double x0 = col[j];
+      const double sigma = fma(x0, x0, t);
+      double beta = 0.0, d = 0.0;
+      if (sigma > 0.0) {
+        const double alpha = sqrt(sigma);
+        const double s = x0 >= 0.0 ? 1.0 : -1.0;
+        const double v0 = x0 + s * alpha;
+        beta = 2.0 / fma(v0, v0, t);
+        d = -s * alpha;
+        col[j] = v0;
+      }
+      s_beta[j] = beta;
+      s_diag[j] = d;
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    s_beta[j] = beta;
-    s_diag[j] = d;
-  }
+  const double beta = s_beta[j];
   if (beta != 0.0) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = j + 1 + warp; c < n; c += nw) {
-      double *ac = A + (int64_t)c * lda;
-      double w = 0.0;
-      for (int i = j + lane; i < k; i += 32) w = fma(col[i], ac[i], w);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      const double bw = beta * w;
-      for (int i = j + lane; i < k; i += 32) ac[i] = fma(-bw, col[i], ac[i]);
+    const int q = threadIdx.x & 3, nq = blockDim.x >> 2;
+    // every warp runs the same iterations (the quad shuffles need all 32 lanes)
+    for (int c0 = j + 1; c0 < n; c0 += nq) {
+      const int c = c0 + (threadIdx.x >> 2);
+      const bool valid = c < n;
+      double *ac = A + (int64_t)(valid ? c : j) * lda;
+      const double w = quad_dot(col, ac, j, valid ? rows : j, q);
+      if (valid) {
+        const double bw = beta * w;
+        for (int i = j + q; i < rows; i += 4) ac[i] = fma(-bw, col[i], ac[i]);
+      }
     }
   }
   __syncthreads();
 }
 
 // S = H_0 ... H_{n-1} [I; 0] from the reflectors stored in A (v in A[j:, j]).
-__device__ void form_S(const double *A, int k, int n, int64_t lda, const double *s_beta,
-                       double *S, int64_t lds) {
-  for (int e = threadIdx.x; e < k * n; e += blockDim.x) {
-    const int i = e % k, c = e / k;
+__device__ void form_S(const double *A, int rows, int n, int lda, const double *s_beta, double *S,
+                       int64_t lds) {
+  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+    const int i = e % rows, c = e / rows;
     S[i + (int64_t)c * lds] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = n - 1; j >= 0; --j) {
     const double beta = s_beta[j];
     if (beta != 0.0) {
       const double *v = A + (int64_t)j * lda;
-      for (int c = j + warp; c < n; c += nw) {
+      for (int c = j + threadIdx.x; c < n; c += blockDim.x) {
         double *sc = S + (int64_t)c * lds;
         double w = 0.0;
-        for (int i = j + lane; i < k; i += 32) w = fma(v[i], sc[i], w);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        for (int i = j; i < rows; ++i) w = fma(v[i], sc[i], w);
         const double bw = beta * w;
-        for (int i = j + lane; i < k; i += 32) sc[i] = fma(-bw, v[i], sc[i]);
+        for (int i = j; i < rows; ++i) sc[i] = fma(-bw, v[i], sc[i]);
       }
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kSmallThreads)
-small_qr_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double *S, int64_t lds,
-                double *R, int64_t ldr, double *gwork, int use_smem) {
-  extern __shared__ double smem[];
-  __shared__ double red[32];
-  __shared__ double s_beta[256], s_diag[256];
-  double *A = use_smem ? smem : gwork;
-  const int64_t lda = k;
-  for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
-    const int i = (int)(e % k), c = (int)(e / k);
-    A[e] = P[i + (int64_t)c * ldp];
+// Copy rows r0..r0+rows-1 of P (ldp) into A (lda), optionally dividing column c by D[c].
+__device__ void load_block(const double *P, int64_t ldp, int r0, int rows, int n, double *A, int lda,
+                           const double *Dc) {
+  for (int64_t e = threadIdx.x; e < (int64_t)rows * n; e += blockDim.x) {
+    const int i = (int)(e % rows), c = (int)(e / rows);
+    double v = P[(r0 + i) + (int64_t)c * ldp];
+    if (Dc) v /= Dc[c];
+    A[i + (int64_t)c * lda] = v;
   }
   __syncthreads();
-  for (int j = 0; j < n; ++j) householder_step(A, k, n, lda, j, red, s_beta, s_diag);
-  // R with positive diagonal: row j negated when d_j < 0 (S's column j with it)
+}
+
+// R (diag >= 0) from the Householder factors: row i negated when s_diag[i] < 0.
+__device__ void store_R(const double *A, int lda, int n, const double *s_diag, double *R, int64_t ldr) {
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e % n, c = e / n;
     const double sg = s_diag[i] < 0.0 ? -1.0 : 1.0;
@@ -111,6 +144,18 @@ small_qr_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double 
     else if (i == c) v = sg * s_diag[i];
     R[i + (int64_t)c * ldr] = v;
   }
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+small_qr_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double *S, int64_t lds,
+                double *R, int64_t ldr, double *gwork, int use_smem) {
+  extern __shared__ double smem[];
+  __shared__ double s_beta[256], s_diag[256];
+  double *A = use_smem ? smem : gwork;
+  const int lda = odd_ld(k);
+  load_block(P, ldp, 0, k, n, A, lda, nullptr);
+  for (int j = 0; j < n; ++j) householder_step(A, k, n, lda, j, s_beta, s_diag);
+  store_R(A, lda, n, s_diag, R, ldr);
   if (S) {
     form_S(A, k, n, lda, s_beta, S, lds);
     for (int e = threadIdx.x; e < k * n; e += blockDim.x) {
@@ -120,50 +165,139 @@ small_qr_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double 
   }
 }
 
+// ---- R only, as a tree (TSQR): Householder QR of L row blocks of P on L CTAs,
+// then the L triangles folded by one CTA.  R is unique once its diagonal is
+// made positive, so it equals the R of Householder on all of P up to rounding.
+__global__ void __launch_bounds__(kSmallThreads)
+tsqr_leaf_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, int L, double *Rleaf,
+                 double *gwork, int use_smem) {
+  extern __shared__ double smem[];
+  __shared__ double s_beta[256], s_diag[256];
+  const int l = blockIdx.x;
+  const int r0 = (int)((int64_t)k * l / L), r1 = (int)((int64_t)k * (l + 1) / L);
+  const int rows = r1 - r0;                       // >= n
+  const int lda = odd_ld(rows);
+  const int64_t per = (int64_t)odd_ld((k + L - 1) / L) * n;
+  double *A = use_smem ? smem : gwork + (int64_t)l * per;
+  load_block(P, ldp, r0, rows, n, A, lda, nullptr);
+  for (int j = 0; j < n; ++j) householder_step(A, rows, n, lda, j, s_beta, s_diag);
+  double *Rl = Rleaf + (int64_t)l * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    Rl[e] = i < c ? A[i + (int64_t)c * lda] : (i == c ? s_diag[i] : 0.0);
+  }
+}
+
+// T <- R of [T; B] for upper triangular n x n T and B (ld n, column-major).
+// The reflector of column j acts on row j of T and rows 0..j of B only.
+__device__ void fold_triangles(double *T, double *B, int n, double *scal) {
+  for (int j = 0; j < n; ++j) {
+    double *bj = B + (int64_t)j * n;
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i <= j; i += 32) t = fma(bj[i], bj[i], t);
+      t = warp0_sum(t);
+      if (threadIdx.x == 0) {
+        const double x0 = T[j + (int64_t)j * n];
+        double beta = 0.0, v0 = 0.0, d = x0;
+        if (t > 0.0) {
+          const double alpha = sqrt(fma(x0, x0, t));
+          const double s = x0 >= 0.0 ? 1.0 : -1.0;
+          v0 = x0 + s * alpha;
+          beta = 2.0 / fma(v0, v0, t);
+          d = -s * alpha;
+        }
+        scal[0] = v0;
+        scal[1] = beta;
+        scal[2] = d;
+      }
+    }
+    __syncthreads();
+    const double v0 = scal[0], beta = scal[1];
+    if (beta != 0.0) {
+      const int q = threadIdx.x & 3, nq = blockDim.x >> 2;
+      for (int c0 = j + 1; c0 < n; c0 += nq) {
+        const int c = c0 + (threadIdx.x >> 2);
+        const bool valid = c < n;
+        double *bc = B + (int64_t)(valid ? c : j) * n;
+        const double tjc = valid ? T[j + (int64_t)c * n] : 0.0;
+        const double w = fma(v0, tjc, quad_dot(bj, bc, 0, valid ? j + 1 : 0, q));
+        if (valid) {
+          const double bw = beta * w;
+          for (int i = q; i <= j; i += 4) bc[i] = fma(-bw, bj[i], bc[i]);
+          if (q == 0) T[j + (int64_t)c * n] = fma(-bw, v0, tjc);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) T[j + (int64_t)j * n] = scal[2];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) bj[i] = 0.0;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+tsqr_fold_kernel(double *Rleaf, int n, int L, double *R, int64_t ldr) {
+  __shared__ double scal[4];
+  for (int l = 1; l < L; ++l) fold_triangles(Rleaf, Rleaf + (int64_t)l * n * n, n, scal);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    const double sg = Rleaf[i + (int64_t)i * n] < 0.0 ? -1.0 : 1.0;
+    R[i + (int64_t)c * ldr] = i <= c ? sg * Rleaf[i + (int64_t)c * n] : 0.0;
+  }
+}
+
 // Column-pivoted QR of P D^{-1} + rank + de-normalised R.
 __global__ void __launch_bounds__(kSmallThreads)
 qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
             double tau, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
             int *dev_status, double *gwork, int use_smem) {
   extern __shared__ double smem[];
-  __shared__ double red[32];
-  __shared__ double s_beta[256], s_diag[256], s_norm[256], s_D[256], s_x[256], s_y[256];
+  __shared__ double s_beta[256], s_diag[256], s_D[256], s_x[256], s_y[256], s_scal[4];
+  __shared__ unsigned long long s_key[256];
   __shared__ int s_perm[256];
   __shared__ int s_piv;
   double *A = use_smem ? smem : gwork;
-  const int64_t lda = k;
+  const int lda = odd_ld(k);
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double d = colnorm2 ? sqrt(colnorm2[c]) : 1.0;
+    const double d = colnorm2 ? sqrt(colnorm2[c]) : 1.0;
     s_D[c] = d > 0.0 ? d : 1.0;
     s_perm[c] = c;
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
-    const int i = (int)(e % k), c = (int)(e / k);
-    A[e] = P[i + (int64_t)c * ldp] / s_D[c];
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  load_block(P, ldp, 0, k, n, A, lda, s_D);
   for (int j = 0; j < n; ++j) {
-    // recomputed norms of the remaining columns (rows j..k-1)
-    for (int c = j + warp; c < n; c += nw) {
+    // recomputed norms of the remaining columns (rows j..k-1), one thread per column;
+    // non-negative doubles order like their bit patterns
+    for (int c = j + threadIdx.x; c < n; c += blockDim.x) {
       const double *ac = A + (int64_t)c * lda;
       double s = 0.0;
-      for (int i = j + lane; i < k; i += 32) s = fma(ac[i], ac[i], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) s_norm[c] = sqrt(s);
+      for (int i = j; i < k; ++i) s = fma(ac[i], ac[i], s);
+      s_key[c] = (unsigned long long)__double_as_longlong(sqrt(s));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int p = j;
-      double best = s_norm[j];
-      for (int c = j + 1; c < n; ++c)
-        if (s_norm[c] > best) {
-          best = s_norm[c];
+    if (threadIdx.x < 32) {
+      // argmax, lowest index on ties
+      unsigned long long best = 0;
+      int p = n;
+      for (int c = j + threadIdx.x; c < n; c += 32) {
+        const unsigned long long kv = s_key[c];
+        if (p == n || kv > best) {
+          best = kv;
           p = c;
         }
-      s_piv = p;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int op = __shfl_down_sync(0xffffffffu, p, o);
+        if (op < n && (p == n || ob > best || (ob == best && op < p))) {
+          best = ob;
+          p = op;
+        }
+      }
+      if (threadIdx.x == 0) s_piv = p;
     }
     __syncthreads();
     const int p = s_piv;
@@ -180,48 +314,46 @@ qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const doubl
       }
     }
     __syncthreads();
-    householder_step(A, k, n, lda, j, red, s_beta, s_diag);
+    householder_step(A, k, n, lda, j, s_beta, s_diag);
   }
-  // R (diag >= 0) into the output buffer, then the rank test on it.
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, c = e / n;
-    const double sg = s_diag[i] < 0.0 ? -1.0 : 1.0;
-    double v = 0.0;
-    if (i < c) v = sg * A[i + (int64_t)c * lda];
-    else if (i == c) v = sg * s_diag[i];
-    R[i + (int64_t)c * ldr] = v;
-  }
+  store_R(A, lda, n, s_diag, R, ldr);
   __syncthreads();
-  // ||R||_2 by 64 steps of power iteration on R^T R from the all-ones vector.
+  // ||R||_2 by 24 steps of power iteration on R^T R from the all-ones vector
   for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = 1.0;
   __syncthreads();
   double norm2 = 0.0;
-  for (int it = 0; it < 64; ++it) {
+  for (int it = 0; it < 24; ++it) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {  // y = R x
       double s = 0.0;
       for (int c = i; c < n; ++c) s = fma(R[i + (int64_t)c * ldr], s_x[c], s);
       s_y[i] = s;
     }
     __syncthreads();
+    if (threadIdx.x < 32) {
+      double yy = 0.0, xx = 0.0;
+      for (int c = threadIdx.x; c < n; c += 32) {
+        yy = fma(s_y[c], s_y[c], yy);
+        xx = fma(s_x[c], s_x[c], xx);
+      }
+      yy = warp0_sum(yy);
+      xx = warp0_sum(xx);
+      if (threadIdx.x == 0) s_scal[0] = xx > 0.0 ? sqrt(yy / xx) : 0.0;   // ||R x|| / ||x||
+    }
     for (int c = threadIdx.x; c < n; c += blockDim.x) {  // x' = R^T y
       double s = 0.0;
       for (int i = 0; i <= c; ++i) s = fma(R[i + (int64_t)c * ldr], s_y[i], s);
-      s_norm[c] = s;
+      s_beta[c] = s;
     }
     __syncthreads();
-    double yy = 0.0, xx = 0.0;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      yy = fma(s_y[c], s_y[c], yy);
-      xx = fma(s_x[c], s_x[c], xx);
+    norm2 = s_scal[0];
+    if (threadIdx.x < 32) {
+      double nn = 0.0;
+      for (int c = threadIdx.x; c < n; c += 32) nn = fma(s_beta[c], s_beta[c], nn);
+      nn = warp0_sum(nn);
+      if (threadIdx.x == 0) s_scal[1] = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
     }
-    yy = block_sum(yy, red);
-    xx = block_sum(xx, red);
-    norm2 = xx > 0.0 ? sqrt(yy / xx) : 0.0;  // ||R x|| / ||x||
-    double nn = 0.0;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) nn = fma(s_norm[c], s_norm[c], nn);
-    nn = block_sum(nn, red);
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = s_norm[c] * inv;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = s_beta[c] * s_scal[1];
     __syncthreads();
   }
   // suffix Frobenius norms: F2[r] = sum_{i>=r} sum_{c>=i} R_ic^2
@@ -235,7 +367,7 @@ qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const doubl
     const double bound = tau * norm2;
     double suffix = 0.0;
     int r = n;
-    // walk r from n down: suffix = F2[r]; keep the least r with sqrt(F2[r]) <= bound
+    // the least r with sqrt(F2[r]) <= bound; F2 is non-increasing in r
     for (int rr = n; rr >= 0; --rr) {
       if (rr < n) suffix += s_y[rr];
       if (sqrt(suffix) <= bound) r = rr;
@@ -259,34 +391,47 @@ qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const doubl
 }
 
 // R' = chol(A[:r,:r]); R[:r, :] <- R' R[:r, :].
+// Left-looking Cholesky: the pivot of row j by warp 0 (one reciprocal), then
+// row j of R' with one thread per column.  The product R' R one 16-column
+// panel of R at a time through shared memory: column c of the new R depends
+// only on column c of the old one, so panels are overwritten in place.
 __global__ void __launch_bounds__(kSmallThreads)
 chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64_t *rank,
                    double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status) {
+  __shared__ double panel[256 * 16];
+  __shared__ double s_scal[2];
   __shared__ int s_fail;
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
   if (threadIdx.x == 0) s_fail = -1;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rp[(e % n) + (int64_t)(e / n) * ldrp] = 0.0;
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    __shared__ double s_d;
-    if (threadIdx.x == 0) {
-      double d = A[j + (int64_t)j * lda];
-      for (int i = 0; i < j; ++i) d -= Rp[i + (int64_t)j * ldrp] * Rp[i + (int64_t)j * ldrp];
-      if (!(d > 0.0)) {
-        s_fail = j;
-        s_d = 0.0;
-      } else {
-        s_d = sqrt(d);
-        Rp[j + (int64_t)j * ldrp] = s_d;
+    const double *cj = Rp + (int64_t)j * ldrp;
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < j; i += 32) t = fma(cj[i], cj[i], t);
+      t = warp0_sum(t);
+      if (threadIdx.x == 0) {
+        const double d = A[j + (int64_t)j * lda] - t;
+        if (!(d > 0.0)) {
+          s_fail = j;
+        } else {
+          const double djj = sqrt(d);
+          Rp[j + (int64_t)j * ldrp] = djj;
+          s_scal[0] = 1.0 / djj;
+        }
       }
     }
     __syncthreads();
     if (s_fail >= 0) break;
-    const double djj = s_d;
-    for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x) {
-      double s = A[j + (int64_t)c * lda];
-      for (int i = 0; i < j; ++i) s -= Rp[i + (int64_t)j * ldrp] * Rp[i + (int64_t)c * ldrp];
-      Rp[j + (int64_t)c * ldrp] = s / djj;
+    const double inv = s_scal[0];
+    const int q = threadIdx.x & 3, nq = blockDim.x >> 2;
+    for (int c0 = j + 1; c0 < r; c0 += nq) {
+      const int c = c0 + (threadIdx.x >> 2);
+      const bool valid = c < r;
+      const double *cc = Rp + (int64_t)(valid ? c : j) * ldrp;
+      const double dot = quad_dot(cj, cc, 0, valid ? j : 0, q);
+      if (valid && q == 0) Rp[j + (int64_t)c * ldrp] = (A[j + (int64_t)c * lda] - dot) * inv;
     }
     __syncthreads();
   }
@@ -297,15 +442,20 @@ chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64
     }
     return;
   }
-  // R[:r, :] <- R' R[:r, :] in place, top row first: new row i reads rows i..r-1
-  // of the old R, which later iterations have not yet overwritten; each thread
-  // owns whole columns, so no other thread reads what it writes.
-  for (int i = 0; i < r; ++i) {
-    for (int c = i + threadIdx.x; c < n; c += blockDim.x) {
+  for (int c0 = 0; c0 < n; c0 += 16) {
+    const int cw = min(16, n - c0);
+    for (int e = threadIdx.x; e < r * cw; e += blockDim.x) {
+      const int i = e % r, c = e / r;
+      panel[c * 256 + i] = R[i + (int64_t)(c0 + c) * ldr];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * cw; e += blockDim.x) {
+      const int i = e % r, c = e / r;
+      const int cg = c0 + c;
+      const int lend = min(cg, r - 1);
       double s = 0.0;
-      const int lend = min(c, r - 1);
-      for (int l = i; l <= lend; ++l) s = fma(Rp[i + (int64_t)l * ldrp], R[l + (int64_t)c * ldr], s);
-      R[i + (int64_t)c * ldr] = s;
+      for (int l = i; l <= lend; ++l) s = fma(Rp[i + (int64_t)l * ldrp], panel[c * 256 + l], s);
+      R[i + (int64_t)cg * ldr] = (cg >= i) ? s : 0.0;
     }
     __syncthreads();
   }
@@ -335,23 +485,42 @@ __global__ void reset_status_kernel(int *st) {
 
 __global__ void set_rank_kernel(int64_t *rank, int64_t v) { *rank = v; }
 
-bool fits_smem(int64_t k, int64_t n) { return (size_t)(k * n) * 8 <= kSmemLimit; }
+size_t copy_bytes(int64_t rows, int64_t n) { return (size_t)((rows | 1) * n) * 8; }
+bool fits_smem(int64_t rows, int64_t n) { return copy_bytes(rows, n) <= kSmemLimit; }
+
+int tsqr_leaves(int64_t k, int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(k / n, 32)); }
 
 }  // namespace
 
 size_t small_qr_workspace(int64_t k, int64_t n) {
+  const int L = tsqr_leaves(k, n);
   Workspace w(nullptr, 0);
-  w.take<double>((size_t)k * n);
-  w.take<double>((size_t)n * n);
+  w.take<double>((size_t)((k + L) | 1) * n + (size_t)2 * L * n);   // working copies
+  w.take<double>((size_t)L * n * n);                                // leaf triangles
   return w.used;
+}
+
+cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, double *R, int64_t ldr,
+                           Workspace &ws, cudaStream_t st) {
+  const int L = tsqr_leaves(k, n);
+  double *g = ws.take<double>((size_t)((k + L) | 1) * n + (size_t)2 * L * n);
+  double *Rleaf = ws.take<double>((size_t)L * n * n);
+  if (!g || !Rleaf) return cudaErrorMemoryAllocation;
+  const int64_t rows_max = (k + L - 1) / L;
+  const bool sm = fits_smem(rows_max, n);
+  const size_t bytes = sm ? copy_bytes(rows_max, n) : 0;
+  if (sm) cudaFuncSetAttribute(tsqr_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  tsqr_leaf_kernel<<<L, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, L, Rleaf, g, sm);
+  tsqr_fold_kernel<<<1, kSmallThreads, 0, st>>>(Rleaf, (int)n, L, R, ldr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, double *S,
                             int64_t lds, double *R, int64_t ldr, Workspace &ws, cudaStream_t st) {
   const bool sm = fits_smem(k, n);
-  double *g = ws.take<double>((size_t)k * n);
+  double *g = ws.take<double>((size_t)(k | 1) * n);
   if (!g) return cudaErrorMemoryAllocation;
-  const size_t bytes = sm ? (size_t)k * n * 8 : 0;
+  const size_t bytes = sm ? copy_bytes(k, n) : 0;
   if (sm) cudaFuncSetAttribute(small_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
   small_qr_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, S, lds, R, ldr, g, sm);
   return cudaGetLastError();
@@ -361,9 +530,9 @@ cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, cons
                         double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         int *dev_status, Workspace &ws, cudaStream_t st) {
   const bool sm = fits_smem(k, n);
-  double *g = ws.take<double>((size_t)k * n);
+  double *g = ws.take<double>((size_t)(k | 1) * n);
   if (!g) return cudaErrorMemoryAllocation;
-  const size_t bytes = sm ? (size_t)k * n * 8 : 0;
+  const size_t bytes = sm ? copy_bytes(k, n) : 0;
   if (sm) cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
   qrcp_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, colnorm2, tau, R, ldr, perm,
                                                rank, dev_status, g, sm);
@@ -371,10 +540,9 @@ cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, cons
 }
 
 cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
-                                  double *Rp, int64_t ldrp, double *R, int64_t ldr,
+                               double *Rp, int64_t ldrp, double *R, int64_t ldr,
                                int *dev_status, cudaStream_t st) {
-  chol_update_kernel<<<1, kSmallThreads, 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, R, ldr,
-                                                  dev_status);
+  chol_update_kernel<<<1, kSmallThreads, 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, R, ldr, dev_status);
   return cudaGetLastError();
 }
 

@@ -118,17 +118,53 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
     for (int b = 0; b < 8; ++b) outer[a][b] = comp[a][b] = 0.0f;
   const int64_t nch = (m + kG32Rows - 1) / kG32Rows;
   const int64_t cb = (nch * g) / groups, ce = (nch * (g + 1)) / groups;
-  for (int64_t ch = cb; ch < ce; ++ch) {
+  const bool diag = bi == bj;
+  const float *qsb = diag ? qa : qb;
+  // chunk loads: thread owns 4 row-quads (4 consecutive rows of one column) per slab,
+  // prefetched into registers one chunk ahead
+  float4 pa[4], pb[4];
+  auto load_chunk = [&](int64_t ch) {
     const int64_t r0 = ch * kG32Rows;
-    __syncthreads();
-    for (int e = tid; e < 64 * kG32Rows; e += 256) {
-      const int rr = e % kG32Rows, c = e / kG32Rows;
-      const int64_t row = r0 + rr;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = tid + 256 * u;
+      const int c = f >> 4, rq = f & 15;
+      const int64_t row = r0 + 4 * rq;
       const int ca = bi * 64 + c, cbb = bj * 64 + c;
-      qa[c * kG32Stride + rr] = (row < m && ca < r) ? Q[row + (int64_t)ca * ldq] : 0.0f;
-      qb[c * kG32Stride + rr] = (row < m && cbb < r) ? Q[row + (int64_t)cbb * ldq] : 0.0f;
+      float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) {
+        if (row + k4 < m) {
+          if (ca < r) va[k4] = Q[row + k4 + (int64_t)ca * ldq];
+          if (!diag && cbb < r) vb[k4] = Q[row + k4 + (int64_t)cbb * ldq];
+        }
+      }
+      pa[u] = make_float4(va[0], va[1], va[2], va[3]);
+      pb[u] = make_float4(vb[0], vb[1], vb[2], vb[3]);
+    }
+  };
+  if (cb < ce) load_chunk(cb);
+  for (int64_t ch = cb; ch < ce; ++ch) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = tid + 256 * u;
+      const int c = f >> 4, rq = f & 15;
+      float *da = qa + c * kG32Stride + 4 * rq;
+      da[0] = pa[u].x;
+      da[1] = pa[u].y;
+      da[2] = pa[u].z;
+      da[3] = pa[u].w;
+      if (!diag) {
+        float *db = qb + c * kG32Stride + 4 * rq;
+        db[0] = pb[u].x;
+        db[1] = pb[u].y;
+        db[2] = pb[u].z;
+        db[3] = pb[u].w;
+      }
     }
     __syncthreads();
+    if (ch + 1 < ce) load_chunk(ch + 1);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -139,7 +175,7 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
 #pragma unroll
       for (int a = 0; a < 4; ++a) va[a] = qa[(ti + 16 * a) * kG32Stride + rr];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) vb[b] = qb[(tj + 8 * b) * kG32Stride + rr];
+      for (int b = 0; b < 8; ++b) vb[b] = qsb[(tj + 8 * b) * kG32Stride + rr];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -235,7 +271,7 @@ cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int 
 int gram32_groups(int64_t m, int64_t n) {
   const int64_t nb = (n + 63) / 64;
   const int64_t tiles = nb * (nb + 1) / 2;
-  int64_t g = std::max<int64_t>(1, (2LL * num_sms()) / tiles);
+  int64_t g = std::max<int64_t>(1, (4LL * num_sms()) / tiles);
   g = std::min<int64_t>(g, std::max<int64_t>(1, (m + kG32Rows - 1) / kG32Rows));
   return (int)std::min<int64_t>(g, 65535);
 }

@@ -105,16 +105,15 @@ gram_partial_kernel(const TQ *__restrict__ Q, int64_t m, int n, int64_t ldq,
   }
 }
 
-// A(i, j) = sum_g partial[g](min, max) (symmetric fill), fixed order.
+// A(i, j) = sum_g partial[g](min, max) (symmetric fill): one warp per entry, fixed order.
 __global__ void gram_reduce_kernel(const double *__restrict__ partial, int groups, int n,
                                    double *__restrict__ A, int64_t lda) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (idx >= (int64_t)n * n) return;
   int i = (int)(idx % n), j = (int)(idx / n);
   const int a = min(i, j), b = max(i, j);
-  double s = 0.0;
-  for (int g = 0; g < groups; ++g) s += partial[((int64_t)g * n + b) * n + a];
-  A[i + (int64_t)j * lda] = s;
+  const double s = warp_sum_strided(partial + (int64_t)b * n + a, groups, (int64_t)n * n);
+  if ((threadIdx.x & 31) == 0) A[i + (int64_t)j * lda] = s;
 }
 
 int gram_groups(int64_t m, int64_t n) {
@@ -173,7 +172,7 @@ cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int pr
     if (!p32) return cudaErrorMemoryAllocation;
     cudaError_t e = launch_gram32((const float *)Q, m, n, ldq, rank, p32, g32, st);
     if (e != cudaSuccess) return e;
-    gram_reduce_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(p32, g32, (int)n, A, lda);
+    gram_reduce_kernel<<<(unsigned)((n * n * 32 + 255) / 256), 256, 0, st>>>(p32, g32, (int)n, A, lda);
     return cudaGetLastError();
   }
   const int groups = gram_groups(m, n);
@@ -187,7 +186,7 @@ cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int pr
   else
     gram_partial_kernel<float><<<grid, 256, 0, st>>>((const float *)Q, m, (int)n, ldq, rank,
                                                      groups, partial);
-  gram_reduce_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(partial, groups, (int)n, A,
+  gram_reduce_kernel<<<(unsigned)((n * n * 32 + 255) / 256), 256, 0, st>>>(partial, groups, (int)n, A,
                                                                       lda);
   return cudaGetLastError();
 }

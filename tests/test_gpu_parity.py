@@ -117,6 +117,18 @@ def test_small_qr_parity(rc, inputs, k, n, cond):
     assert np.all(np.diag(host64(R)) >= 0)
 
 
+@pytest.mark.parametrize("k,n,cond", [(8, 1, 1.0), (72, 16, 1e4), (256, 64, 1e8), (520, 130, 1e10),
+                                      (263, 7, 1e12), (2048, 256, 1e3)])
+def test_small_r_tree_parity(rc, inputs, k, n, cond):
+    # R without S: the TSQR tree (leaf Householder QRs, then folds of stacked triangles)
+    P = inputs.svd_matrix(k, n, cond, 19 + n, dtype="f64", device=DEV)
+    R = rc.rcqr_small_qr(P, want_S=False)
+    torch.cuda.synchronize()
+    _, Ro = olin.householder_qr(host64(P))
+    assert colrel(host64(R), Ro) <= max(1e-12, 10 * n * U * cond)
+    assert np.all(np.diag(host64(R)) >= 0) and np.all(np.tril(host64(R), -1) == 0)
+
+
 def test_qrcp_parity_planted_rank(rc, inputs):
     m, n, r, k = 4000, 24, 12, 96
     X = inputs.rank_deficient(m, n, r, 21, noise=1e-12, dtype="f64", device=DEV)
