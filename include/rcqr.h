@@ -174,6 +174,45 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
                          double *Z, int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
                          void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
+/* One problem of a batched call (all pointers device, owned by the caller;
+ * the fields mean what the arguments of the same names mean in rcqr_factor;
+ * dev_status is this problem's device int[2]). */
+typedef struct {
+  const void *X;
+  int64_t m, n, ldx, k;
+  uint64_t seed;
+  void *Q;
+  int64_t ldq;
+  double *R;
+  int64_t ldr;
+  int32_t *perm;   /* RR variants only, else nullable */
+  int64_t *rank;   /* nullable */
+  int *dev_status;
+} rcqr_problem;
+
+/* Workspace bytes for rcqr_factor_batched on these problems (host array). 0 on
+ * invalid sizes. */
+size_t rcqr_batched_workspace_size(const rcqr_problem *probs, int count, int variant, int prec);
+
+/* Many factorizations (rcqr_factor, same variant, precision and tau for all)
+ * of uneven sizes in one stream-ordered call: `probs` is a HOST array of count
+ * problems; problem i uses Theta with Philox stream index i.  The problems are
+ * spread over library-owned streams forked from `stream` by an event and
+ * joined back, so the call can be recorded by a stream capture on `stream`
+ * (make the first call on a device before capturing: it creates the streams
+ * and loads constants).  Q must not alias X.  Argument errors of any problem
+ * return RCQR_EINVAL before anything is queued. */
+rcqr_status rcqr_factor_batched(const rcqr_problem *probs, int count, int variant, int prec, double tau,
+                                void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Time rcqr_factor_batched on these problems for 1, 2, 4, 8 and 16 streams
+ * (synchronises `stream`), keep the fastest for later calls on this device and
+ * write it to the JSON file named by the environment variable RCQR_TUNE_CACHE
+ * when that is set (read back by later processes).  *best_streams (host)
+ * receives the choice. */
+rcqr_status rcqr_tune_batched(const rcqr_problem *probs, int count, int variant, int prec, double tau,
+                              void *workspace, size_t ws_bytes, cudaStream_t stream, int *best_streams);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,9 +63,9 @@ def rcholqr_from_sketch(X, P):
     return Q, S, R
 
 
-def rcholqr(X, k, seed):
+def rcholqr(X, k, seed, stream=0):
     """Alg. 2: returns (Q, S, R)."""
-    P = sketch(X, k, seed)
+    P = sketch(X, k, seed, stream=stream)
     return rcholqr_from_sketch(X, P)
 
 
@@ -76,9 +76,9 @@ def cholqr_pass(Q, R):
     return linalg.forward_substitution(Q, Rp), Rp @ R, Rp
 
 
-def rcholqr2(X, k, seed):
+def rcholqr2(X, k, seed, stream=0):
     """Alg. 3: returns (Q, R, S) -- S is the orthonormal sketch from the first pass."""
-    Q, S, R = rcholqr(X, k, seed)
+    Q, S, R = rcholqr(X, k, seed, stream)
     Q2, R2, _ = cholqr_pass(Q, R)
     return Q2, R2, S
 
@@ -93,7 +93,7 @@ def reduced(X, k, seed, L=None):
     return Z, S, R
 
 
-def rrrcholqr(X, k, seed, tau):
+def rrrcholqr(X, k, seed, tau, stream=0):
     """Alg. 7 with column normalisation: returns (Q m x r, S k x r, R r x n, perm, r).
 
     X[:, perm] ~ Q R.  Zero columns of X are left unscaled (D_j = 1 for them).
@@ -101,7 +101,7 @@ def rrrcholqr(X, k, seed, tau):
     X = np.asarray(X, dtype=np.float64)
     D = column_norms(X)
     Dsafe = np.where(D > 0, D, 1.0)
-    P = sketch(X, k, seed) / Dsafe[None, :]                  # P <- P D^{-1}
+    P = sketch(X, k, seed, stream=stream) / Dsafe[None, :]   # P <- P D^{-1}
     S, R, perm = linalg.qrcp(P)                               # step 2
     r = linalg.truncation_rank(R, tau)                        # step 3
     Xsel = X[:, perm[:r]] / Dsafe[perm[:r]][None, :]          # X Pi_{:,1:r} D_sel^{-1}
@@ -110,9 +110,9 @@ def rrrcholqr(X, k, seed, tau):
     return Q, S[:, :r], Rout, perm, r
 
 
-def rrrcholqr2(X, k, seed, tau):
+def rrrcholqr2(X, k, seed, tau, stream=0):
     """Alg. 7 followed by one CholeskyQR pass: returns (Q, R, perm, r)."""
-    Q, _, R, perm, r = rrrcholqr(X, k, seed, tau)
+    Q, _, R, perm, r = rrrcholqr(X, k, seed, tau, stream)
     if r == 0:
         return Q, R, perm, r
     Q2, R2, _ = cholqr_pass(Q, R)

@@ -217,3 +217,66 @@ def rcqr_reduced(X, k, seed, L=None, want_S=True):
                                             _ld(S) if S is not None else 0, _ptr(R), _ld(R), wp, wb,
                                             _ptr(status), _stream()))
     return Z, S, R, status
+
+
+class rcqr_problem(ctypes.Structure):
+    _fields_ = [("X", _vp), ("m", _i64), ("n", _i64), ("ldx", _i64), ("k", _i64), ("seed", _u64),
+                ("Q", _vp), ("ldq", _i64), ("R", _vp), ("ldr", _i64), ("perm", _vp), ("rank", _vp),
+                ("dev_status", _vp)]
+
+
+lib.rcqr_batched_workspace_size.restype = _sz
+lib.rcqr_batched_workspace_size.argtypes = [_vp, _i32, _i32, _i32]
+lib.rcqr_factor_batched.restype = _i32
+lib.rcqr_factor_batched.argtypes = [_vp, _i32, _i32, _i32, _dbl, _vp, _sz, _vp]
+lib.rcqr_tune_batched.restype = _i32
+lib.rcqr_tune_batched.argtypes = [_vp, _i32, _i32, _i32, _dbl, _vp, _sz, _vp, _vp]
+
+
+class Batch:
+    """Device buffers and the host problem array of one batched call (kept alive together)."""
+
+    def __init__(self, Xs, ks, seed, variant, tau=0.0):
+        self.Xs = Xs
+        self.variant, self.tau = variant, float(tau)
+        self.prec = prec_of(Xs[0].dtype)
+        dev = Xs[0].device
+        qdt = torch.float64 if self.prec == F64 else torch.float32
+        rr = variant in (RR, RR2)
+        self.Qs, self.Rs, self.perms, self.ranks = [], [], [], []
+        self.status = torch.zeros((len(Xs), 2), dtype=torch.int32, device=dev)
+        arr = (rcqr_problem * len(Xs))()
+        for i, (X, k) in enumerate(zip(Xs, ks)):
+            m, n = X.shape
+            Q = colmajor(m, n, qdt, dev)
+            R = colmajor(n, n, torch.float64, dev)
+            perm = torch.empty(n, dtype=torch.int32, device=dev) if rr else None
+            rank = torch.empty(1, dtype=torch.int64, device=dev)
+            self.Qs.append(Q), self.Rs.append(R), self.perms.append(perm), self.ranks.append(rank)
+            arr[i] = rcqr_problem(X.data_ptr(), m, n, _ld(X), k, seed, Q.data_ptr(), _ld(Q), R.data_ptr(), _ld(R),
+                                  perm.data_ptr() if perm is not None else None, rank.data_ptr(),
+                                  self.status[i].data_ptr())
+        self.arr = arr
+        nbytes = lib.rcqr_batched_workspace_size(ctypes.cast(arr, _vp), len(Xs), variant, self.prec)
+        if nbytes == 0:
+            raise RcqrError("rcqr_batched_workspace_size", -1)
+        self.ws = _workspace(nbytes, dev)
+
+    def run(self):
+        wp, wb = _aligned_ptr(self.ws)
+        _check("rcqr_factor_batched", lib.rcqr_factor_batched(ctypes.cast(self.arr, _vp), len(self.Xs), self.variant,
+                                                              self.prec, self.tau, wp, wb, _stream()))
+
+    def tune(self):
+        wp, wb = _aligned_ptr(self.ws)
+        best = ctypes.c_int(0)
+        _check("rcqr_tune_batched", lib.rcqr_tune_batched(ctypes.cast(self.arr, _vp), len(self.Xs), self.variant,
+                                                          self.prec, self.tau, wp, wb, _stream(), ctypes.byref(best)))
+        return best.value
+
+
+def rcqr_factor_batched(Xs, ks, seed, variant=RR, tau=0.0):
+    """Factor every X in Xs (problem i uses Theta stream i); returns the Batch with Qs, Rs, perms, ranks, status."""
+    b = Batch(Xs, ks, seed, variant, tau)
+    b.run()
+    return b

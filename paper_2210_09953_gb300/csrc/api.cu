@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "rcqr_internal.h"
 
@@ -21,6 +22,20 @@ int num_sms() {
     count[dev] = c;
   }
   return count[dev];
+}
+
+cudaError_t ensure_smem(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void *, int>, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto &d : done)
+    if (d.first.first == func && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.push_back({{func, dev}, bytes});
+  return e;
 }
 
 namespace {
@@ -188,6 +203,20 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         uint64_t seed, int variant, double tau, void *Q, int64_t ldq, double *R,
                         int64_t ldr, int32_t *perm, int64_t *rank, void *workspace,
                         size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  return rcqr::factor_impl(X, m, n, ldx, prec, k, seed, 0u, variant, tau, Q, ldq, R, ldr, perm, rank,
+                           workspace, ws_bytes, dev_status, stream);
+}
+
+}  // extern "C"
+
+namespace rcqr {
+
+// The factorization with Theta's Philox stream index (0 for single calls, the
+// problem index in the batched call).
+rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                        uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
+                        int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
   if (!X || !Q || !R || !dev_status || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m ||
       ldq < m || ldr < n || variant < 0 || variant > 3)
     return RCQR_EINVAL;
@@ -217,7 +246,7 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
 
   RCQR_TRY(launch_reset_status(dev_status, stream));
   // Alg. 2 / Alg. 7 step 1 (with D of Sec. 4 in the same pass for RR)
-  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, rr ? b.colnorm2 : nullptr,
+  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, stream_id, 0, b.P, k, rr ? b.colnorm2 : nullptr,
                          *scratch(), stream, dev_status));
   const int32_t *pm = nullptr;
   const int64_t *rkp = nullptr;
@@ -245,6 +274,10 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
 #undef RCQR_TRY
   return RCQR_OK;
 }
+
+}  // namespace rcqr
+
+extern "C" {
 
 rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                          uint64_t seed, const double *L, int64_t l, int64_t ldl, double *Z,

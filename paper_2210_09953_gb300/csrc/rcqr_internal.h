@@ -38,6 +38,20 @@ struct Workspace {
 
 int num_sms();
 
+// Raise a kernel's dynamic shared-memory limit on the current device, once:
+// later calls (for instance inside a stream capture) make no CUDA call.
+cudaError_t ensure_smem(const void *func, int bytes);
+template <class K>
+inline cudaError_t set_smem(K *kernel, int bytes) {
+  return ensure_smem(reinterpret_cast<const void *>(kernel), bytes);
+}
+
+// rcqr_factor with Theta's Philox stream index (0 for single calls).
+rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                        uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
+                        int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
 inline size_t elem_size(int prec) { return prec == RCQR_F64 ? 8 : (prec == RCQR_F32 ? 4 : 2); }
 inline size_t q_elem_size(int prec) { return prec == RCQR_F64 ? 8 : 4; }
 

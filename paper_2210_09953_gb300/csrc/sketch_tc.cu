@@ -476,7 +476,7 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
 template <int PREC, int KCH, int JCH>
 cudaError_t launch_tc_variant(const TcArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
   auto kern = sketch_tc_kernel<PREC, KCH, JCH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem(kern, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreadsTC, smem, st>>>(a);
   return cudaGetLastError();

@@ -509,7 +509,7 @@ cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, d
   const int64_t rows_max = (k + L - 1) / L;
   const bool sm = fits_smem(rows_max, n);
   const size_t bytes = sm ? copy_bytes(rows_max, n) : 0;
-  if (sm) cudaFuncSetAttribute(tsqr_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (sm) set_smem(tsqr_leaf_kernel, (int)kSmemLimit);
   tsqr_leaf_kernel<<<L, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, L, Rleaf, g, sm);
   tsqr_fold_kernel<<<1, kSmallThreads, 0, st>>>(Rleaf, (int)n, L, R, ldr);
   return cudaGetLastError();
@@ -521,7 +521,7 @@ cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, 
   double *g = ws.take<double>((size_t)(k | 1) * n);
   if (!g) return cudaErrorMemoryAllocation;
   const size_t bytes = sm ? copy_bytes(k, n) : 0;
-  if (sm) cudaFuncSetAttribute(small_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (sm) set_smem(small_qr_kernel, (int)kSmemLimit);
   small_qr_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, S, lds, R, ldr, g, sm);
   return cudaGetLastError();
 }
@@ -533,7 +533,7 @@ cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, cons
   double *g = ws.take<double>((size_t)(k | 1) * n);
   if (!g) return cudaErrorMemoryAllocation;
   const size_t bytes = sm ? copy_bytes(k, n) : 0;
-  if (sm) cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (sm) set_smem(qrcp_kernel, (int)kSmemLimit);
   qrcp_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, colnorm2, tau, R, ldr, perm,
                                                rank, dev_status, g, sm);
   return cudaGetLastError();

@@ -221,8 +221,7 @@ cudaError_t launch_trsm32_t(const TX *X, int64_t m, int64_t n, int64_t ldx, cons
   const size_t smem = (size_t)NB * NB * 4 + (size_t)NB * 4;
 #define RCQR_T32(NBV)                                                                                       \
   case NBV: {                                                                                               \
-    cudaError_t e = cudaFuncSetAttribute(trsm32_kernel<TX, NBV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                         (int)smem);                                                        \
+    cudaError_t e = set_smem(trsm32_kernel<TX, NBV>, (int)smem);                                           \
     if (e != cudaSuccess) return e;                                                                         \
     trsm32_kernel<TX, NBV><<<blocks, kT32Threads, smem, st>>>(X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq); \
     break;                                                                                                  \
