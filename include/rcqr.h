@@ -174,6 +174,22 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
                          double *Z, int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
                          void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
+/* Reverse mode of RCholeskyQR2 (the paper has no counterpart: differentiation
+ * is an addition of this library).  In exact arithmetic Alg. 3 returns the
+ * unique thin QR of X (Q orthonormal, diag(R) > 0) whatever Theta is, so its
+ * derivative is that of the thin QR map:
+ *   M = R Rbar^T - Qbar^T Q,  Xbar = (Qbar + Q copyltu(M)) R^{-T},
+ *   copyltu(M) = tril(M) + tril(M, -1)^T.
+ * Q: the factor recomputed from X and the stored R (rcqr_trsm), m x n; Qbar
+ * (same type as Q), Rbar (double, n x n, upper triangle used) the incoming
+ * gradients; Xbar (type of Q) receives the gradient.  prec: RCQR_F64 (double
+ * data, FP64) or RCQR_F32 (float data, FP32 rows with a compensated Qbar^T Q).
+ * Workspace: rcqr_qr_adjoint_workspace_size(m, n) bytes. */
+size_t rcqr_qr_adjoint_workspace_size(int64_t m, int64_t n);
+rcqr_status rcqr_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *R,
+                            int64_t ldr, const void *Qbar, int64_t ldqb, const double *Rbar, int64_t ldrb,
+                            void *Xbar, int64_t ldxb, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* One problem of a batched call (all pointers device, owned by the caller;
  * the fields mean what the arguments of the same names mean in rcqr_factor;
  * dev_status is this problem's device int[2]). */

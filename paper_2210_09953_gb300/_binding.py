@@ -280,3 +280,22 @@ def rcqr_factor_batched(Xs, ks, seed, variant=RR, tau=0.0):
     b = Batch(Xs, ks, seed, variant, tau)
     b.run()
     return b
+
+
+lib.rcqr_qr_adjoint_workspace_size.restype = _sz
+lib.rcqr_qr_adjoint_workspace_size.argtypes = [_i64, _i64]
+lib.rcqr_qr_adjoint.restype = _i32
+lib.rcqr_qr_adjoint.argtypes = [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                                _sz, _vp]
+
+
+def rcqr_qr_adjoint(Q, R, Qbar, Rbar):
+    """Xbar of the thin QR map for the factors (Q, R) and incoming gradients (Qbar, Rbar)."""
+    m, n = Q.shape
+    prec = F64 if Q.dtype == torch.float64 else F32
+    Xbar = colmajor(m, n, Q.dtype, Q.device)
+    ws = _workspace(lib.rcqr_qr_adjoint_workspace_size(m, n), Q.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_qr_adjoint", lib.rcqr_qr_adjoint(_ptr(Q), m, n, _ld(Q), prec, _ptr(R), _ld(R), _ptr(Qbar), _ld(Qbar),
+                                                  _ptr(Rbar), _ld(Rbar), _ptr(Xbar), _ld(Xbar), wp, wb, _stream()))
+    return Xbar

@@ -279,6 +279,22 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
 
 extern "C" {
 
+size_t rcqr_qr_adjoint_workspace_size(int64_t m, int64_t n) {
+  if (m < 1 || n < 1 || n > 256) return 0;
+  return adjoint_workspace(m, n) + 256;
+}
+
+rcqr_status rcqr_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *R,
+                            int64_t ldr, const void *Qbar, int64_t ldqb, const double *Rbar, int64_t ldrb,
+                            void *Xbar, int64_t ldxb, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!Q || !R || !Qbar || !Rbar || !Xbar || !(prec == RCQR_F64 || prec == RCQR_F32) || m < 1 || n < 1 ||
+      n > 256 || ldq < m || ldqb < m || ldxb < m || ldr < n || ldrb < n)
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < adjoint_workspace(m, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_qr_adjoint(Q, m, n, ldq, prec, R, ldr, Qbar, ldqb, Rbar, ldrb, Xbar, ldxb, w, stream));
+}
+
 rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                          uint64_t seed, const double *L, int64_t l, int64_t ldl, double *Z,
                          int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,

@@ -117,6 +117,11 @@ cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int 
 int gram32_groups(int64_t m, int64_t n);
 cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
                           double *partial, int groups, cudaStream_t st);
+// Reverse mode of the thin QR map (adjoint.cu).
+size_t adjoint_workspace(int64_t m, int64_t n);
+cudaError_t launch_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *R,
+                              int64_t ldr, const void *Qbar, int64_t ldqb, const double *Rbar, int64_t ldrb,
+                              void *Xbar, int64_t ldxb, Workspace &ws, cudaStream_t st);
 size_t gram_workspace(int64_t m, int64_t n);
 cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
                         const int64_t *rank, double *A, int64_t lda, Workspace &ws,

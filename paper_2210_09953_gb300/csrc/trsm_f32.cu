@@ -94,19 +94,26 @@ constexpr int kG32Stride = 65;   // column stride in shared memory (conflict-fre
 // A entries (bi*64 + ti + 16a, bj*64 + tj + 8b), a < 4, b < 8.
 __global__ void __launch_bounds__(256)
 gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const int64_t *__restrict__ rank,
-              int groups, double *__restrict__ partial) {
+              int groups, double *__restrict__ partial, const float *__restrict__ Q2, int64_t ldq2) {
   // two 64-column slabs of the chunk (column-major, stride 65), reused for the final reduction
   __shared__ double smd[64 * kG32Stride];
   float *qa = reinterpret_cast<float *>(smd);
   float *qb = qa + 64 * kG32Stride;
   double *red = smd;                         // 128 x 32 doubles <= 2 x 64 x 65 floats
   const int nb = (n + 63) / 64;
-  int t = blockIdx.x, bi = 0;
-  while (t >= nb - bi) {
-    t -= nb - bi;
-    ++bi;
+  // Q2 == nullptr: the Gram Q^T Q, upper tiles only; else Q^T Q2, every tile
+  int bi = 0, bj = 0;
+  if (Q2) {
+    bi = blockIdx.x % nb;
+    bj = blockIdx.x / nb;
+  } else {
+    int t = blockIdx.x;
+    while (t >= nb - bi) {
+      t -= nb - bi;
+      ++bi;
+    }
+    bj = bi + t;
   }
-  const int bj = bi + t;
   const int g = blockIdx.y;
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
   const int tid = threadIdx.x, grp = tid >> 7, lt = tid & 127;
@@ -118,8 +125,10 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
     for (int b = 0; b < 8; ++b) outer[a][b] = comp[a][b] = 0.0f;
   const int64_t nch = (m + kG32Rows - 1) / kG32Rows;
   const int64_t cb = (nch * g) / groups, ce = (nch * (g + 1)) / groups;
-  const bool diag = bi == bj;
+  const bool diag = bi == bj && Q2 == nullptr;
   const float *qsb = diag ? qa : qb;
+  const float *Qb = Q2 ? Q2 : Q;
+  const int64_t ldb = Q2 ? ldq2 : ldq;
   // chunk loads: thread owns 4 row-quads (4 consecutive rows of one column) per slab,
   // prefetched into registers one chunk ahead
   float4 pa[4], pb[4];
@@ -136,7 +145,7 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
       for (int k4 = 0; k4 < 4; ++k4) {
         if (row + k4 < m) {
           if (ca < r) va[k4] = Q[row + k4 + (int64_t)ca * ldq];
-          if (!diag && cbb < r) vb[k4] = Q[row + k4 + (int64_t)cbb * ldq];
+          if (!diag && cbb < r) vb[k4] = Qb[row + k4 + (int64_t)cbb * ldb];
         }
       }
       pa[u] = make_float4(va[0], va[1], va[2], va[3]);
@@ -279,7 +288,23 @@ cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, con
                           double *partial, int groups, cudaStream_t st) {
   const int64_t nb = (n + 63) / 64;
   dim3 grid((unsigned)(nb * (nb + 1) / 2), (unsigned)groups);
-  gram32_kernel<<<grid, 256, 0, st>>>(Q, m, (int)n, ldq, rank, groups, partial);
+  gram32_kernel<<<grid, 256, 0, st>>>(Q, m, (int)n, ldq, rank, groups, partial, nullptr, 0);
+  return cudaGetLastError();
+}
+
+int cross_gram32_groups(int64_t m, int64_t n) {
+  const int64_t nb = (n + 63) / 64;
+  int64_t g = std::max<int64_t>(1, (4LL * num_sms()) / (nb * nb));
+  g = std::min<int64_t>(g, std::max<int64_t>(1, (m + kG32Rows - 1) / kG32Rows));
+  return (int)std::min<int64_t>(g, 65535);
+}
+
+// partial[g] (n x n, column-major) = rows of range g of A^T B, FP32 A and B.
+cudaError_t launch_cross_gram32(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t m,
+                                int64_t n, double *partial, int groups, cudaStream_t st) {
+  const int64_t nb = (n + 63) / 64;
+  dim3 grid((unsigned)(nb * nb), (unsigned)groups);
+  gram32_kernel<<<grid, 256, 0, st>>>(A, m, (int)n, lda, nullptr, groups, partial, B, ldb);
   return cudaGetLastError();
 }
 
