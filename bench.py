@@ -261,7 +261,9 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sketch_bytes = m * N * 4                 # algorithmic: X read once
     achieved = sketch_bytes / (ms_sketch * 1e-3) / 1e9
-    launches_per_step = 10                   # reset, sketch x2, small QR, rank, TRSM, Gram x2, Cholesky, TRSM
+    # per factorization (mixed path, Alg. 3): status reset, sketch + its reduction, TSQR leaves + fold,
+    # rank, TRSM prep + rows, Gram + reduction, Cholesky update, TRSM prep + rows
+    launches_per_step = 13
 
     if rank == 0:
         cpu = None
