@@ -2,29 +2,38 @@
 //
 // Theta's entries are the integer levels T[t] in [-127, 127] (scaled by
 // 1/sqrt(k v) afterwards), i.e. 7-bit integers, exact in bf16.  X is cut, per
-// 1024-row block and column, into S signed 7-bit integer slices relative to
-// the block's largest exponent e (x = sum_b s_b 2^(e-6-7b) + a remainder below
-// the last slice; an error-free splitting in the manner of Ozaki et al.).
-// Each slice is a bf16 operand; every product T*s is an integer below 2^14,
-// so the fp32 tensor-core sums over at most 1024 rows stay below 2^24 and
-// are exact.  The first NE slices get their own TMEM accumulators (exact);
-// the remaining ones, pre-scaled by 2^-7 per slice, share one accumulator
-// whose fp32 rounding over a block stays ~2^-39 (FP32 X: 3 exact of 5
-// slices) / 2^-46 (FP64 X: 4 exact of 8) below the block's largest |x|;
-// BF16 X needs 3 slices and its last one alone is exact as well.
-// After every block the accumulators are read from TMEM, combined into one
-// int64 per entry and added into a per-column block-floating-point int64
-// accumulator in registers (the "simple addition" of Sec. 3.1 done exactly,
-// up to one truncation of ~2^-52 relative per block).
+// 1024-row block and column, into S signed digit slices relative to the
+// block's largest exponent e: with t = x 2^(6-e) in (-128, 128), slice b holds
+// a multiple of 2^(-7b) of magnitude <= 128 2^(-7b) (an error-free splitting
+// in the manner of Ozaki et al.; round-to-nearest digits for FP32/BF16 X,
+// truncated 7-bit digits of the FP64 significand).  Each slice is a bf16
+// operand with at most 8 significant bits, every product T*d is below 2^14
+// units of its slice, so the fp32 tensor-core sums over 1024 rows stay below
+// 2^24 units and are exact.  The first NE slices get their own TMEM
+// accumulators (exact); the remaining ones share one accumulator whose fp32
+// rounding over a block stays ~2^-39 (FP32 X: 3 exact of 5 slices) / 2^-46
+// (FP64 X: 4 exact of 8) below the block's largest |x|; BF16 X needs 3
+// slices.  After every block the accumulators are read from TMEM, combined
+// into one int64 per entry and added into a per-column block-floating-point
+// int64 accumulator (the "simple addition" of Sec. 3.1 done exactly, up to
+// one truncation of ~2^-52 relative per block).
 //
 // Per CTA: a contiguous run of blocks (split-K over m), KCH chunks of 128
-// rows of Theta and NC columns of X.  Per stage of BK rows: all 512 threads
-// generate the Theta tile (Philox4x32-10 + level table) and the X slices in
-// shared memory in the K-major core-matrix layout; one thread issues the
-// MMAs (M = 128, N = NC, K = 16) and commits them to the stage's mbarrier;
-// two stages let the tensor core work on one while the CUDA cores fill the
-// other.  Every wait is bounded; a timeout marks the partial sums NaN and
-// raises RCQR_ETIMEOUT in the status word.
+// rows of Theta and NC columns of X.  The CTA is warp-specialised around a
+// ring of D shared-memory stages of 32 rows each:
+//   * 7 Theta warps generate the Theta tile of a stage (Philox4x32-10 and the
+//     level table, replicated per lane) in the K-major core-matrix layout;
+//   * 8 X warps load the X rows of the stage (prefetched one stage ahead),
+//     cut them into slices, and read the same rows of the next block to find
+//     its column exponents one block ahead;
+//   * one MMA warp waits for a stage to be full, issues its MMAs
+//     (M = 128, N = NC, K = 16) from one thread and commits them to the
+//     stage's "empty" barrier (and after a block's last stage, to the
+//     "accumulators full" barrier).
+// At a block boundary every warp folds TMEM into the int64 accumulators (kept
+// in the workspace, L2-resident) once the producers have filled the first D
+// stages of the next block.  Every wait is bounded; a timeout marks the
+// partial sums NaN and raises RCQR_ETIMEOUT in the status word.
 #include <algorithm>
 
 #include "common.cuh"
@@ -38,29 +47,38 @@ __constant__ int8_t c_theta_levels[256];
 
 namespace {
 
-constexpr int kThreadsTC = 512;
-constexpr int kBlockRows = 1024;      // rows per exponent block / TMEM promotion
-constexpr int kStages = 2;
+constexpr int kThetaWarps = 7;                      // Theta tile producers
+constexpr int kXWarps = 8;                          // X slice producers
+constexpr int kProdWarps = kThetaWarps + kXWarps;   // all of them arrive on "full"
+constexpr int kThreadsTC = 32 * (kProdWarps + 1);   // + the MMA warp
+constexpr int kBlockRows = 1024;                    // rows per exponent block / TMEM promotion
+constexpr int kBK = 32;                             // rows of X per stage
+constexpr int kSPB = kBlockRows / kBK;              // stages per block
+constexpr int kMaxStages = 6;
+constexpr int kTableBytes = 256 * 32 * 4;           // level table, one copy per lane
 constexpr uint32_t kWaitPolls = 1u << 26;
 
 template <int PREC>
 struct SliceCfg;
-// S slices; the first NE have exact accumulators, the rest share one (weights
-// 2^-7 apart); LS fractional bits of that shared accumulator are kept in the
-// int64 sum.  Headroom: 24 + 7 NE + LS + log2(MAXB) <= 62 bits.
+// S slices; the first NE have exact accumulators, the rest share one; LS
+// fractional bits of that shared accumulator are kept in the int64 sum.
+// Headroom: 24 + 7 NE + LS + log2(MAXB) <= 62 bits.
 template <>
 struct SliceCfg<RCQR_F64> {
   using T = double;
+  using MaxT = unsigned long long;
   static constexpr int S = 8, NE = 4, LS = 4, MAXB = 64;
 };
 template <>
 struct SliceCfg<RCQR_F32> {
   using T = float;
+  using MaxT = uint32_t;
   static constexpr int S = 5, NE = 3, LS = 10, MAXB = 128;
 };
 template <>
 struct SliceCfg<RCQR_BF16> {
   using T = __nv_bfloat16;
+  using MaxT = uint32_t;
   static constexpr int S = 3, NE = 2, LS = 8, MAXB = 128;
 };
 
@@ -73,39 +91,82 @@ struct TcArgs {
   uint64_t seed;
   uint32_t stream_id;
   int64_t row_offset;
-  int64_t blk0;    // first 1024-row block (global index)
-  int64_t nblk;    // blocks covering [row_offset, row_offset + m)
-  int groups;      // CTAs along m
-  int NC;          // columns per CTA (multiple of 16)
-  int ngrp;        // column groups
-  int KCH;         // 128-row chunks of Theta per CTA
-  int BK;          // rows per stage (16, 32 or 64)
-  double *partial; // [groups][n][k]
-  int *status;     // nullable
+  int64_t blk0;       // first 1024-row block (global index)
+  int64_t nblk;       // blocks covering [row_offset, row_offset + m)
+  int groups;         // CTAs along m
+  int ngrp;           // column groups
+  int D;              // pipeline stages
+  int vec;            // X rows may be read 16 bytes at a time
+  double *partial;    // [groups][n][k]
+  long long *acc64;   // int64 accumulators, KCH * NC * 128 per CTA
+  int *status;        // nullable
 };
 
 constexpr int EMPTY_EXP = -0x40000000;
 
-__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
-
-// Exponent of the largest |x| of a block column: returns EMPTY_EXP for an all-zero column.
-__device__ __forceinline__ int block_exp_f32(uint32_t maxbits) {
+// Exponent of the largest |x| of a block column (from its magnitude bits):
+// EMPTY_EXP for an all-zero (or subnormal-only) column.
+__device__ __forceinline__ int block_exp(uint32_t maxbits) {
   const int be = (int)(maxbits >> 23);
-  return be == 0 ? EMPTY_EXP : be - 127;     // zero or subnormal-only column: treated as zero
+  return be == 0 ? EMPTY_EXP : be - 127;
 }
-__device__ __forceinline__ int block_exp_f64(unsigned long long maxbits) {
+__device__ __forceinline__ int block_exp(unsigned long long maxbits) {
   const int be = (int)((maxbits >> 52) & 0x7FF);
   return be == 0 ? EMPTY_EXP : be - 1023;
 }
 
+__device__ __forceinline__ uint32_t mag_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+__device__ __forceinline__ uint32_t mag_bits(__nv_bfloat16 x) {
+  return ((uint32_t)__bfloat16_as_ushort(x) & 0x7FFFu) << 16;
+}
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
+// 8 consecutive rows lr0 .. lr0+7 of column j (zeros outside X).
+template <class T>
+__device__ __forceinline__ void load8(const T *__restrict__ X, int64_t lr0, int j, const TcArgs &a, T (&v)[8]) {
+  if (j < a.n && a.vec && lr0 >= 0 && lr0 + 8 <= a.m) {
+    const T *p = X + lr0 + (int64_t)j * a.ldx;
+    if constexpr (sizeof(T) == 4) {
+      const float4 u0 = __ldg(reinterpret_cast<const float4 *>(p));
+      const float4 u1 = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+      v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+      v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+    } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const double2 u = __ldg(reinterpret_cast<const double2 *>(p) + h);
+        v[2 * h] = u.x;
+        v[2 * h + 1] = u.y;
+      }
+    } else {
+      const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        v[2 * h] = __ushort_as_bfloat16((unsigned short)(w[h] & 0xFFFFu));
+        v[2 * h + 1] = __ushort_as_bfloat16((unsigned short)(w[h] >> 16));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int64_t lr = lr0 + t;
+      v[t] = (j < a.n && lr >= 0 && lr < a.m) ? X[lr + (int64_t)j * a.ldx] : T(0);
+    }
+  }
+}
+
 // Writes the S slices of 8 consecutive rows of one column (bf16, 16 bytes per
-// slice) to dst + b * slice_stride.  e is the block's column exponent.
+// slice) to dst + b * slice_stride; slice b carries the multiple of 2^(-7b)
+// of x 2^(6-e) described above.  e is the block's column exponent.
 template <int PREC>
 __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&x)[8], int e, unsigned char *dst,
                                              int slice_stride) {
-  constexpr int S = SliceCfg<PREC>::S, NE = SliceCfg<PREC>::NE;
+  constexpr int S = SliceCfg<PREC>::S;
   if constexpr (PREC == RCQR_F64) {
     unsigned long long F[8];
     uint32_t neg = 0;
@@ -120,29 +181,29 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
         const int d = e - (be - 1023);           // >= 0: x is not larger than the block maximum
         f = d <= 3 ? (mant << (3 - d)) : (d - 3 < 64 ? (mant >> (d - 3)) : 0ull);
       }
-      F[t] = f;                                  // |x| * 2^(55-e), below 2^56
+      F[t] = f;                                  // |x| 2^(55-e), below 2^56
     }
 #pragma unroll
     for (int b = 0; b < S; ++b) {
       uint32_t w[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        uint32_t h[2];
+        float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int t = 2 * p + q;
           const uint32_t dig = (uint32_t)(F[t] >> (49 - 7 * b)) & 127u;
-          float v = __uint_as_float(0x4B000000u | dig) - 8388608.0f;   // the digit, exactly
-          if (b >= NE) v *= pow2f(-7 * (b - NE));
-          if ((neg >> t) & 1u) v = -v;
-          h[q] = __float_as_uint(v) >> 16;
+          float dv = __uint_as_float(0x4B000000u | dig) - 8388608.0f;   // the digit, exactly
+          if (b > 0) dv *= pow2f(-7 * b);
+          v[q] = ((neg >> t) & 1u) ? -dv : dv;
         }
-        w[p] = h[0] | (h[1] << 16);
+        w[p] = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
       }
       *reinterpret_cast<uint4 *>(dst + b * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   } else {
-    // FP32 / BF16 storage: scale into (-128, 128) and peel off rounded 7-bit digits
+    // FP32 / BF16 storage: t = x 2^(6-e); digit b = t rounded to a multiple of
+    // 2^(-7b) by adding and removing 1.5 2^(23-7b); t -= digit (both exact)
     float t8[8];
     const int sh = 6 - e;
     const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
@@ -153,275 +214,376 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
         xv = __bfloat162float(x[t]);
       else
         xv = x[t];
-      if (e == EMPTY_EXP || abs_bits(xv) < 0x00800000u) xv = 0.0f;
+      if (e == EMPTY_EXP || mag_bits(xv) < 0x00800000u) xv = 0.0f;
       t8[t] = (xv * s1) * s2;
     }
 #pragma unroll
     for (int b = 0; b < S; ++b) {
+      const float M = __uint_as_float(((uint32_t)(150 - 7 * b) << 23) | 0x400000u);   // 1.5 2^(23-7b)
+      float d[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        d[t] = __fadd_rn(__fadd_rn(t8[t], M), -M);
+        if (b + 1 < S) t8[t] = __fadd_rn(t8[t], -d[t]);
+      }
       uint32_t w[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        uint32_t h[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int t = 2 * p + q;
-          const float d = rintf(t8[t]);
-          if (b + 1 < S) t8[t] = (t8[t] - d) * 128.0f;
-          float v = d;
-          if (b >= NE) v *= pow2f(-7 * (b - NE));
-          h[q] = __float_as_uint(v) >> 16;
-        }
-        w[p] = h[0] | (h[1] << 16);
-      }
+      for (int p = 0; p < 4; ++p) w[p] = __byte_perm(__float_as_uint(d[2 * p]), __float_as_uint(d[2 * p + 1]), 0x7632);
       *reinterpret_cast<uint4 *>(dst + b * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
 
+// The Theta tile of one stage: KCH * 128 rows of Theta x 32 rows of X, one
+// Philox call per 16 X rows.  tt indexes the Theta threads.
+template <int KCH>
+__device__ __forceinline__ void theta_tile(unsigned char *sA, const uint32_t *tabp, int tt, int64_t r0, int kgi,
+                                           const TcArgs &a) {
+  constexpr int cpr = kBK / 16;
+  constexpr int calls = KCH * 128 * cpr;
+#pragma unroll 2
+  for (int ci = tt; ci < calls; ci += 32 * kThetaWarps) {
+    const int qq = ci % cpr, row = ci / cpr;
+    const int c = row >> 7, il = row & 127;
+    const int i = (kgi * KCH + c) * 128 + il;
+    uint32_t wv[8];
+    if (i < a.k) {
+      const uint4 w = theta_block((uint64_t)(r0 / 16 + qq), (uint32_t)i, a.stream_id, a.seed);
+      const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const uint32_t word = ww[p >> 1];
+        const uint32_t b0 = __byte_perm(word, 0u, 0x4440u + 2u * (p & 1));
+        const uint32_t b1 = __byte_perm(word, 0u, 0x4441u + 2u * (p & 1));
+        wv[p] = __byte_perm(tabp[b0 << 5], tabp[b1 << 5], 0x5410);
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) wv[p] = 0u;
+    }
+    unsigned char *dst = sA + c * (128 * kBK * 2) + (il >> 3) * (kBK * 16) + (il & 7) * 16;
+    *reinterpret_cast<uint4 *>(dst + (2 * qq) * 128) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    *reinterpret_cast<uint4 *>(dst + (2 * qq + 1) * 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+  }
+}
+
+// Bounded mbarrier wait that gives up at once when another thread of the CTA
+// has already timed out (so one failure costs one timeout, not one per stage).
+__device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int *fail) {
+  volatile int *f = fail;
+  for (uint32_t round = 0; round < (kWaitPolls >> 10); ++round) {
+    if (*f) return;
+    if (umma::mbar_wait(bar, parity, 1024)) return;
+  }
+  *f = 1;
+}
+
+// Stage after which the producers fold block b: D stages into block b + 1
+// (the ring is then full and waits for the MMAs of block b + 1), or the end.
+__device__ __forceinline__ int epilogue_trigger(int b, int NB, int D) {
+  return b + 1 < NB ? (b + 1) * kSPB + D - 1 : NB * kSPB - 1;
+}
+
+template <int PREC, int KCH, int JCH>
+struct Tc {
+  using Cfg = SliceCfg<PREC>;
+  using T = typename Cfg::T;
+  using MaxT = typename Cfg::MaxT;
+  static constexpr int S = Cfg::S, NE = Cfg::NE, LS = Cfg::LS;
+  static constexpr int NACC = NE + 1;
+  static constexpr int NC = 64 * JCH;                 // columns per CTA
+  static constexpr int CW = NC / 4;                   // columns per thread in the fold
+  static constexpr uint32_t NCOLS = (KCH * NACC * NC) <= 256 ? 256u : 512u;
+  static constexpr int A_BYTES = KCH * 128 * kBK * 2;
+  static constexpr int B_BYTES = S * NC * kBK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static_assert(KCH * NACC * NC <= 512, "TMEM holds 512 columns");
+
+  struct Shared {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t accf;
+    uint32_t tslot;
+    int s_fail;
+    int e_col[2][NC];    // column exponents of the blocks in flight (by block parity)
+    int E_col[2][NC];    // running exponents of the int64 accumulators (by block parity)
+  };
+
+  // Folds block b's TMEM accumulators into the int64 accumulators (all threads).
+  static __device__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc, const TcArgs &a, int kgi,
+                              int col0, int g) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail);
+    umma::fence_after_sync();
+    const bool last = b == NB - 1;
+    const int p = b & 1;
+    if (warp < 16) {
+      const int lq = warp & 3, cq = warp >> 2;
+      const int il = 32 * lq + lane;
+#pragma unroll 1
+      for (int jc0 = 0; jc0 < CW; jc0 += 8) {
+#pragma unroll
+        for (int c = 0; c < KCH; ++c) {
+          uint32_t rv[NACC][8];
+#pragma unroll
+          for (int acc = 0; acc < NACC; ++acc)
+            umma::tmem_ld8(tbase + ((uint32_t)(32 * lq) << 16) + (uint32_t)((c * NACC + acc) * NC + cq * CW + jc0),
+                           rv[acc]);
+          umma::tmem_wait_ld();
+          const int i = (kgi * KCH + c) * 128 + il;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int jl = cq * CW + jc0 + jj;
+            const int e = sh.e_col[p][jl];
+            const int Ec = sh.E_col[p][jl];
+            long long *ap = Acc + ((size_t)c * NC + jl) * 128 + il;
+            long long acc_v;
+            int En;
+            if (e == EMPTY_EXP) {
+              if (!last) continue;
+              En = Ec;
+              acc_v = Ec == EMPTY_EXP ? 0LL : *ap;
+            } else {
+              long long V = 0;
+#pragma unroll
+              for (int bs = 0; bs < NE; ++bs)
+                V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
+              V += __float2ll_rn(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));
+              const int f = e - 6 - 7 * NE - LS;
+              if (Ec == EMPTY_EXP) {
+                acc_v = V;
+                En = f;
+              } else if (f >= Ec) {
+                const int s = f - Ec;
+                const long long old = *ap;
+                acc_v = (s >= 63 ? (old < 0 ? -1LL : 0LL) : (old >> s)) + V;
+                En = f;
+              } else {
+                const int s = Ec - f;
+                acc_v = *ap + (s >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> s));
+                En = Ec;
+              }
+            }
+            if (last) {
+              const int j = col0 + jl;
+              if (i < a.k && j < a.n)
+                a.partial[((int64_t)g * a.n + j) * a.k + i] = En == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, En);
+            } else {
+              *ap = acc_v;
+            }
+          }
+        }
+      }
+    }
+    // running exponents after this block
+    for (int jl = tid; jl < NC; jl += kThreadsTC) {
+      const int e = sh.e_col[p][jl], Ec = sh.E_col[p][jl];
+      int En = Ec;
+      if (e != EMPTY_EXP) {
+        const int f = e - 6 - 7 * NE - LS;
+        En = (Ec == EMPTY_EXP || f > Ec) ? f : Ec;
+      }
+      sh.E_col[p ^ 1][jl] = En;
+    }
+    umma::fence_before_sync();
+    umma::named_sync(kThreadsTC);
+  }
+};
+
 template <int PREC, int KCH, int JCH>
 __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
-  using T = typename SliceCfg<PREC>::T;
-  constexpr int S = SliceCfg<PREC>::S, NE = SliceCfg<PREC>::NE, LS = SliceCfg<PREC>::LS;
-  constexpr int NACC = NE + 1;
-  constexpr int NC = 64 * JCH;                 // columns per CTA
-  constexpr int CW = 16 * JCH;                 // columns per thread in the promotion
-  constexpr uint32_t NCOLS = (KCH * NACC * NC) <= 256 ? 256u : 512u;
-  static_assert(KCH * NACC * NC <= 512, "TMEM holds 512 columns");
-  static_assert(24 + 7 * NE + LS + 7 <= 62 || SliceCfg<PREC>::MAXB <= 64, "int64 headroom");
+  using K = Tc<PREC, KCH, JCH>;
+  using T = typename K::T;
+  using MaxT = typename K::MaxT;
+  constexpr int NC = K::NC, S = K::S;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kStages];
-  __shared__ uint32_t tslot;
-  __shared__ int e_col[NC];        // this block's column exponents
-  __shared__ int E_col[NC];        // running exponents of the int64 accumulators
-  __shared__ int s_fail;
+  __shared__ typename K::Shared sh;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int BK = a.BK;
+  const int D = a.D;
   const int g = blockIdx.y;
   const int kgi = blockIdx.x / a.ngrp, ngi = blockIdx.x % a.ngrp;
   const int col0 = ngi * NC;
   const T *X = static_cast<const T *>(a.X);
-
-  // shared memory: level table replicated per lane (bank = lane), then the stages
   uint32_t *table = reinterpret_cast<uint32_t *>(smem_raw);
-  unsigned char *stage_base = smem_raw + 256 * 32 * 4;
-  const int a_bytes = KCH * 128 * BK * 2;
-  const int b_bytes = S * NC * BK * 2;
-  const int stage_bytes = a_bytes + b_bytes;
+  unsigned char *stage_base = smem_raw + kTableBytes;
 
-  for (int e = tid; e < 256 * 32; e += blockDim.x) {
+  for (int e = tid; e < 256 * 32; e += kThreadsTC) {
     const int lev = (int)c_theta_levels[e >> 5];
     table[e] = __float_as_uint((float)lev) >> 16;
   }
-  for (int j = tid; j < NC; j += blockDim.x) E_col[j] = EMPTY_EXP;
+  for (int j = tid; j < NC; j += kThreadsTC) sh.E_col[0][j] = EMPTY_EXP;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) umma::mbar_init(&bars[s], 1);
-    s_fail = 0;
+    for (int s = 0; s < kMaxStages; ++s) {
+      umma::mbar_init(&sh.full[s], kProdWarps);
+      umma::mbar_init(&sh.empty[s], 1);
+    }
+    umma::mbar_init(&sh.accf, 1);
+    sh.s_fail = 0;
   }
-  if (warp == 0) umma::tmem_alloc(&tslot, NCOLS);
-  umma::fence_before_sync();
-  __syncthreads();
-  umma::fence_after_sync();
-  const uint32_t tbase = tslot;
-
-  // this thread's accumulators: TMEM lane 32*(warp%4)+lane (a row of Theta within
-  // each chunk) and columns [cq*CW, cq*CW+CW)
-  const int lq = warp & 3, cq = warp >> 2;
-  long long A[KCH][CW];
-#pragma unroll
-  for (int c = 0; c < KCH; ++c)
-#pragma unroll
-    for (int j = 0; j < CW; ++j) A[c][j] = 0;
+  if (warp == 0) umma::tmem_alloc(&sh.tslot, K::NCOLS);
 
   const int64_t bb = a.blk0 + (a.nblk * g) / a.groups;
   const int64_t be_ = a.blk0 + (a.nblk * (g + 1)) / a.groups;
-  const uint32_t idesc = umma::idesc_bf16_f32(128, NC);
-  const int steps_per_block = kBlockRows / BK;
-  int it = 0;
+  const int NB = (int)(be_ - bb);
+  const int total = NB * kSPB;
+  long long *Acc = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (KCH * NC * 128);
 
-  for (int64_t blk = bb; blk < be_; ++blk) {
-    const int64_t grow0 = blk * kBlockRows;
-    // ---- exponent pass: the largest |x| of each column over the block
-    for (int jl = warp; jl < NC; jl += kThreadsTC / 32) {
-      const int j = col0 + jl;
-      if constexpr (PREC == RCQR_F64) {
-        unsigned long long mx = 0;
-        if (j < a.n)
-          for (int r = lane; r < kBlockRows; r += 32) {
-            const int64_t lr = grow0 + r - a.row_offset;
-            if (lr >= 0 && lr < a.m) {
-              const unsigned long long bits = (unsigned long long)__double_as_longlong(X[lr + (int64_t)j * a.ldx]);
-              mx = max(mx, bits & 0x7FFFFFFFFFFFFFFFull);
-            }
-          }
+  // X warps: this thread's columns and 8-row octet within a stage
+  const bool is_x = warp >= kThetaWarps && warp < kProdWarps;
+  const int xw = warp - kThetaWarps;
+  const int oc = lane >> 3;
+  int jl_u[JCH];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) e_col[jl] = block_exp_f64(mx);
-      } else {
-        uint32_t mx = 0;
-        if (j < a.n)
-          for (int r = lane; r < kBlockRows; r += 32) {
-            const int64_t lr = grow0 + r - a.row_offset;
-            if (lr >= 0 && lr < a.m) {
-              float v;
-              if constexpr (PREC == RCQR_BF16)
-                v = __bfloat162float(X[lr + (int64_t)j * a.ldx]);
-              else
-                v = X[lr + (int64_t)j * a.ldx];
-              mx = max(mx, abs_bits(v));
-            }
-          }
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) e_col[jl] = block_exp_f32(mx);
-      }
-    }
-    __syncthreads();
+  for (int u = 0; u < JCH; ++u) jl_u[u] = 64 * u + 8 * xw + (lane & 7);
 
-    for (int st = 0; st < steps_per_block; ++st, ++it) {
-      const int sidx = it % kStages;
-      unsigned char *sA = stage_base + sidx * stage_bytes;
-      unsigned char *sB = sA + a_bytes;
-      if (it >= kStages) {
-        if (!umma::mbar_wait(&bars[sidx], (uint32_t)((it / kStages - 1) & 1), kWaitPolls)) s_fail = 1;
-      }
-      const int64_t r0 = grow0 + (int64_t)st * BK;
-      // ---- Theta tile: KCH*128 rows x BK columns, 16 columns per Philox call
-      const int cpr = BK / 16;
-      for (int cidx = tid; cidx < KCH * 128 * cpr; cidx += kThreadsTC) {
-        const int qq = cidx % cpr;
-        const int row = cidx / cpr;
-        const int c = row >> 7, il = row & 127;
-        const int i = (kgi * KCH + c) * 128 + il;
-        uint32_t wv[8];
-        if (i < a.k) {
-          const uint4 w = theta_block((uint64_t)(r0 / 16 + qq), (uint32_t)i, a.stream_id, a.seed);
-          const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+  // exponents of the first block
+  if (is_x) {
+    MaxT mx[JCH];
 #pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const uint32_t b0 = (ww[p >> 1] >> (16 * (p & 1))) & 0xFFu;
-            const uint32_t b1 = (ww[p >> 1] >> (16 * (p & 1) + 8)) & 0xFFu;
-            wv[p] = table[b0 * 32 + lane] | (table[b1 * 32 + lane] << 16);
-          }
-        } else {
+    for (int u = 0; u < JCH; ++u) mx[u] = 0;
+    for (int st = 0; st < kSPB; ++st) {
 #pragma unroll
-          for (int p = 0; p < 8; ++p) wv[p] = 0u;
-        }
-        unsigned char *dst = sA + c * (128 * BK * 2) + (il >> 3) * (BK * 16) + (il & 7) * 16;
-        *reinterpret_cast<uint4 *>(dst + (2 * qq) * 128) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-        *reinterpret_cast<uint4 *>(dst + (2 * qq + 1) * 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-      }
-      // ---- X slices: S operands of NC x BK; one thread per 8-row octet of a column
-      const int opc = BK / 8;
-      for (int o = tid; o < NC * opc; o += kThreadsTC) {
-        const int oc = o % opc, jl = o / opc;
-        const int j = col0 + jl;
-        T xv[8];
+      for (int u = 0; u < JCH; ++u) {
+        T v[8];
+        load8<T>(X, bb * kBlockRows + st * kBK + 8 * oc - a.row_offset, col0 + jl_u[u], a, v);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int64_t lr = r0 + 8 * oc + t - a.row_offset;
-          xv[t] = (j < a.n && lr >= 0 && lr < a.m) ? X[lr + (int64_t)j * a.ldx] : T(0);
-        }
-        unsigned char *dst = sB + (jl >> 3) * (BK * 16) + oc * 128 + (jl & 7) * 16;
-        slice8_store<PREC>(xv, j < a.n ? e_col[jl] : EMPTY_EXP, dst, NC * BK * 2);
-      }
-      umma::fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        umma::fence_after_sync();
-        const uint32_t a0 = umma::smem_u32(sA), b0 = umma::smem_u32(sB);
-#pragma unroll
-        for (int c = 0; c < KCH; ++c)
-#pragma unroll
-          for (int b = 0; b < S; ++b) {
-            const int acc = b < NE ? b : NE;
-            const uint32_t dcol = tbase + (uint32_t)((c * NACC + acc) * NC);
-            for (int q = 0; q < BK / 16; ++q) {
-              const uint64_t ad = umma::smem_desc(a0 + c * (128 * BK * 2) + q * 256, 128, BK * 16);
-              const uint64_t bd = umma::smem_desc(b0 + b * (NC * BK * 2) + q * 256, 128, BK * 16);
-              const bool first = (st == 0) && (q == 0) && (b <= NE);
-              umma::mma_bf16(dcol, ad, bd, idesc, first ? 0u : 1u);
-            }
-          }
-        umma::mma_commit(&bars[sidx]);
+        for (int t = 0; t < 8; ++t) mx[u] = max(mx[u], mag_bits(v[t]));
       }
     }
-    // ---- promotion: wait for the block's last MMAs, fold TMEM into the int64 accumulators
-    {
-      const int last = (it - 1) % kStages;
-      if (!umma::mbar_wait(&bars[last], (uint32_t)(((it - 1) / kStages) & 1), kWaitPolls)) s_fail = 1;
+#pragma unroll
+    for (int u = 0; u < JCH; ++u) {
+      mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 8));
+      mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 16));
+      if (oc == 0) sh.e_col[0][jl_u[u]] = col0 + jl_u[u] < a.n ? block_exp(mx[u]) : EMPTY_EXP;
     }
-    umma::fence_after_sync();
-#pragma unroll
-    for (int jc0 = 0; jc0 < CW; jc0 += 16) {
-#pragma unroll
-      for (int c = 0; c < KCH; ++c) {
-        uint32_t rv[NACC][16];
-#pragma unroll
-        for (int acc = 0; acc < NACC; ++acc)
-          umma::tmem_ld16(tbase + ((uint32_t)(32 * lq) << 16) + (uint32_t)((c * NACC + acc) * NC + cq * CW + jc0),
-                          rv[acc]);
-        umma::tmem_wait_ld();
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int jl = cq * CW + jc0 + jj;
-          const int e = e_col[jl];
-          if (e == EMPTY_EXP) continue;
-          long long V = 0;
-#pragma unroll
-          for (int b = 0; b < NE; ++b)
-            V += (long long)__float2int_rn(__uint_as_float(rv[b][jj])) << (7 * (NE - b) + LS);
-          V += __float2ll_rn(__uint_as_float(rv[NE][jj]) * (float)(1 << LS));
-          const int f = e - 6 - 7 * NE - LS;
-          const int Ec = E_col[jl];
-          long long acc_v = A[c][jc0 + jj];
-          if (Ec == EMPTY_EXP) {
-            acc_v = V;
-          } else if (f >= Ec) {
-            const int sh = f - Ec;
-            acc_v = (sh >= 63 ? (acc_v < 0 ? -1LL : 0LL) : (acc_v >> sh)) + V;
-          } else {
-            const int sh = Ec - f;
-            acc_v += sh >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> sh);
-          }
-          A[c][jc0 + jj] = acc_v;
-        }
-      }
-    }
-    umma::fence_before_sync();
-    __syncthreads();
-    // running exponent of each column: the larger of the old one and this block's frame
-    for (int jl = tid; jl < NC; jl += blockDim.x) {
-      const int e = e_col[jl];
-      if (e == EMPTY_EXP) continue;
-      const int f = e - 6 - 7 * NE - LS;
-      if (E_col[jl] == EMPTY_EXP || f > E_col[jl]) E_col[jl] = f;
-    }
-    __syncthreads();
-  }
-
-  // ---- this CTA's partial sketch: partial[g][j][i]
-  const bool failed = s_fail != 0;
-#pragma unroll
-  for (int c = 0; c < KCH; ++c) {
-    const int i = (kgi * KCH + c) * 128 + lq * 32 + lane;
-#pragma unroll
-    for (int jc = 0; jc < CW; ++jc) {
-      const int jl = cq * CW + jc;
-      const int j = col0 + jl;
-      if (i >= a.k || j >= a.n) continue;
-      const int Ec = E_col[jl];
-      double v = Ec == EMPTY_EXP ? 0.0 : ldexp((double)A[c][jc], Ec);
-      if (failed) v = __longlong_as_double(0x7FF8000000000000ll);
-      a.partial[((int64_t)g * a.n + j) * a.k + i] = v;
-    }
-  }
-  if (failed && tid == 0 && a.status) {
-    a.status[0] = RCQR_ETIMEOUT;
-    a.status[1] = -1;
   }
   umma::fence_before_sync();
   __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tbase, NCOLS);
+  umma::fence_after_sync();
+  const uint32_t tbase = sh.tslot;
+
+  if (warp < kThetaWarps) {
+    // ---- Theta producers
+    const uint32_t *tabp = table + lane;
+    int next = 0;
+    for (int it = 0; it < total; ++it) {
+      const int slot = it % D;
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail);
+      const int b = it / kSPB, st = it % kSPB;
+      theta_tile<KCH>(stage_base + slot * K::STAGE_BYTES, tabp, tid, (bb + b) * kBlockRows + st * kBK, kgi, a);
+      umma::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
+      if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
+    }
+  } else if (is_x) {
+    // ---- X producers
+    T cur[JCH][8], nxt[JCH][8];
+    MaxT mx[JCH];
+#pragma unroll
+    for (int u = 0; u < JCH; ++u) {
+      mx[u] = 0;
+      load8<T>(X, bb * kBlockRows + 8 * oc - a.row_offset, col0 + jl_u[u], a, cur[u]);
+    }
+    int next = 0;
+    for (int it = 0; it < total; ++it) {
+      const int slot = it % D;
+      const int b = it / kSPB, st = it % kSPB;
+      const int64_t r0 = (bb + b) * kBlockRows + st * kBK;
+      const bool more_blocks = b + 1 < NB;
+      if (it + 1 < total) {
+        const int64_t r1 = (bb + (it + 1) / kSPB) * kBlockRows + ((it + 1) % kSPB) * kBK;
+#pragma unroll
+        for (int u = 0; u < JCH; ++u) load8<T>(X, r1 + 8 * oc - a.row_offset, col0 + jl_u[u], a, nxt[u]);
+      }
+      T ex[JCH][8];
+      if (more_blocks) {
+#pragma unroll
+        for (int u = 0; u < JCH; ++u) load8<T>(X, r0 + kBlockRows + 8 * oc - a.row_offset, col0 + jl_u[u], a, ex[u]);
+      }
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail);
+      unsigned char *sB = stage_base + slot * K::STAGE_BYTES + K::A_BYTES;
+      const int p = b & 1;
+#pragma unroll
+      for (int u = 0; u < JCH; ++u) {
+        const int jl = jl_u[u];
+        slice8_store<PREC>(cur[u], sh.e_col[p][jl], sB + (jl >> 3) * (kBK * 16) + oc * 128 + (jl & 7) * 16,
+                           NC * kBK * 2);
+      }
+      umma::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
+      if (more_blocks) {
+#pragma unroll
+        for (int u = 0; u < JCH; ++u)
+#pragma unroll
+          for (int t = 0; t < 8; ++t) mx[u] = max(mx[u], mag_bits(ex[u][t]));
+        if (st == kSPB - 1) {
+#pragma unroll
+          for (int u = 0; u < JCH; ++u) {
+            mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 8));
+            mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 16));
+            if (oc == 0) sh.e_col[p ^ 1][jl_u[u]] = col0 + jl_u[u] < a.n ? block_exp(mx[u]) : EMPTY_EXP;
+            mx[u] = 0;
+          }
+          __syncwarp();
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < JCH; ++u)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cur[u][t] = nxt[u][t];
+      if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
+    }
+  } else {
+    // ---- MMA warp: one thread issues, the warp folds with the others
+    const uint32_t idesc = umma::idesc_bf16_f32(128, NC);
+    for (int it = 0; it < total; ++it) {
+      const int slot = it % D;
+      const int b = it / kSPB, st = it % kSPB;
+      if (lane == 0) {
+        wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail);
+        umma::fence_after_sync();
+        const uint32_t a0 = umma::smem_u32(stage_base + slot * K::STAGE_BYTES);
+        const uint32_t b0 = a0 + K::A_BYTES;
+#pragma unroll
+        for (int c = 0; c < KCH; ++c)
+#pragma unroll
+          for (int bs = 0; bs < S; ++bs) {
+            const int acc = bs < K::NE ? bs : K::NE;
+            const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + acc) * NC);
+#pragma unroll
+            for (int q = 0; q < kBK / 16; ++q) {
+              const uint64_t ad = umma::smem_desc(a0 + c * (128 * kBK * 2) + q * 256, 128, kBK * 16);
+              const uint64_t bd = umma::smem_desc(b0 + bs * (NC * kBK * 2) + q * 256, 128, kBK * 16);
+              const bool first = (st == 0) && (q == 0) && (bs <= K::NE);
+              umma::mma_bf16(dcol, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        umma::mma_commit(&sh.empty[slot]);
+        if (st == kSPB - 1) umma::mma_commit(&sh.accf);
+      }
+      __syncwarp();
+      if (st == kSPB - 1) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g);
+    }
+  }
+
+  // every thread has passed the last fold's barrier: all MMAs and TMEM reads are done
+  if (*(volatile int *)&sh.s_fail != 0) {
+    for (int e = tid; e < KCH * 128 * NC; e += kThreadsTC) {
+      const int il = e % (KCH * 128), jl = e / (KCH * 128);
+      const int i = kgi * KCH * 128 + il, j = col0 + jl;
+      if (i < a.k && j < a.n) a.partial[((int64_t)g * a.n + j) * a.k + i] = __longlong_as_double(0x7FF8000000000000ll);
+    }
+    if (tid == 0 && a.status) {
+      a.status[0] = RCQR_ETIMEOUT;
+      a.status[1] = -1;
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tbase, K::NCOLS);
 }
 
 // P(i, j) = c * sum_g partial[g](i, j): one warp per entry, fixed order.
@@ -435,7 +597,7 @@ __global__ void sketch_tc_reduce_kernel(const double *__restrict__ partial, int 
 }
 
 struct TcPlan {
-  int JCH, NC, ngrp, KCH, kgrp, BK, groups, S;
+  int JCH, NC, ngrp, KCH, kgrp, D, groups, S;
   int64_t blk0, nblk;
   size_t smem;
 };
@@ -455,14 +617,11 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   const int kchunks = (int)((k + 127) / 128);
   p.KCH = (p.JCH == 1 && kchunks >= 2 && 2 * nacc * 64 <= 512) ? 2 : 1;
   p.kgrp = (kchunks + p.KCH - 1) / p.KCH;
-  // rows per stage: the largest of 64/32/16 whose two stages fit beside the table
-  const size_t table = 256 * 32 * 4;
-  p.BK = 64;
-  auto bytes = [&](int bk) {
-    return table + (size_t)kStages * ((size_t)p.KCH * 128 * bk * 2 + (size_t)p.S * p.NC * bk * 2);
-  };
-  while (p.BK > 16 && bytes(p.BK) > 200 * 1024) p.BK /= 2;
-  p.smem = bytes(p.BK);
+  // as many 32-row stages as fit beside the level table (at most kMaxStages)
+  const size_t stage = (size_t)p.KCH * 128 * kBK * 2 + (size_t)p.S * p.NC * kBK * 2;
+  const size_t budget = 220 * 1024 - kTableBytes;
+  p.D = (int)std::min<size_t>(kMaxStages, budget / stage);
+  p.smem = kTableBytes + (size_t)p.D * stage;
   p.blk0 = row_offset / kBlockRows;
   p.nblk = (row_offset + m + kBlockRows - 1) / kBlockRows - p.blk0;
   const int64_t ctas_per_rows = (int64_t)p.kgrp * p.ngrp;
@@ -471,6 +630,10 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   groups = std::max<int64_t>(groups, (p.nblk + maxb - 1) / maxb);
   p.groups = (int)std::min<int64_t>(groups, 65535);
   return p;
+}
+
+size_t acc64_count(const TcPlan &p) {
+  return (size_t)p.groups * p.kgrp * p.ngrp * p.KCH * p.NC * 128;
 }
 
 template <int PREC, int KCH, int JCH>
@@ -504,6 +667,7 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, 
   const TcPlan p = plan_tc(m, n, k, row_offset, prec);
   Workspace w(nullptr, 0);
   w.take<double>((size_t)p.groups * n * k);
+  w.take<long long>(acc64_count(p));
   return w.used;
 }
 
@@ -520,7 +684,8 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   }
   const TcPlan p = plan_tc(m, n, k, row_offset, prec);
   double *partial = ws.take<double>((size_t)p.groups * n * k);
-  if (!partial) return cudaErrorMemoryAllocation;
+  long long *acc64 = ws.take<long long>(acc64_count(p));
+  if (!partial || !acc64) return cudaErrorMemoryAllocation;
   TcArgs a;
   a.X = X;
   a.m = m;
@@ -533,11 +698,12 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   a.blk0 = p.blk0;
   a.nblk = p.nblk;
   a.groups = p.groups;
-  a.NC = p.NC;
   a.ngrp = p.ngrp;
-  a.KCH = p.KCH;
-  a.BK = p.BK;
+  a.D = p.D;
+  const size_t es = elem_size(prec);
+  a.vec = ((uintptr_t)X % 16 == 0) && ((size_t)ldx * es) % 16 == 0 && ((size_t)row_offset * es) % 16 == 0;
   a.partial = partial;
+  a.acc64 = acc64;
   a.status = dev_status;
   dim3 grid((unsigned)(p.kgrp * p.ngrp), (unsigned)p.groups);
   cudaError_t e;
