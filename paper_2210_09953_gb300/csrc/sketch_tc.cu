@@ -21,11 +21,11 @@
 // Per CTA: a contiguous run of blocks (split-K over m), KCH chunks of 128
 // rows of Theta and NC columns of X.  The CTA is warp-specialised around a
 // ring of D shared-memory stages of 32 rows each:
-//   * 7 Theta warps generate the Theta tile of a stage (Philox4x32-10 and the
+//   * 8 Theta warps generate the Theta tile of a stage (Philox4x32-10 and the
 //     level table, replicated per lane) in the K-major core-matrix layout;
-//   * 8 X warps load the X rows of the stage (prefetched one stage ahead),
-//     cut them into slices, and read the same rows of the next block to find
-//     its column exponents one block ahead;
+//   * 7 X warps copy the X rows of a stage three stages ahead into a small
+//     ring (cp.async, no registers held), then cut them into slices with the
+//     block's column exponents (found beforehand by block_exp_kernel);
 //   * one MMA warp waits for a stage to be full, issues its MMAs
 //     (M = 128, N = NC, K = 16) from one thread and commits them to the
 //     stage's "empty" barrier (and after a block's last stage, to the
@@ -47,8 +47,8 @@ __constant__ int8_t c_theta_levels[256];
 
 namespace {
 
-constexpr int kThetaWarps = 7;                      // Theta tile producers
-constexpr int kXWarps = 8;                          // X slice producers
+constexpr int kThetaWarps = 8;                      // Theta tile producers
+constexpr int kXWarps = 7;                          // X slice producers
 constexpr int kProdWarps = kThetaWarps + kXWarps;   // all of them arrive on "full"
 constexpr int kThreadsTC = 32 * (kProdWarps + 1);   // + the MMA warp
 constexpr int kBlockRows = 1024;                    // rows per exponent block / TMEM promotion
@@ -56,7 +56,9 @@ constexpr int kBK = 32;                             // rows of X per stage
 constexpr int kSPB = kBlockRows / kBK;              // stages per block
 constexpr int kMaxStages = 6;
 constexpr int kTableBytes = 256 * 32 * 4;           // level table, one copy per lane
-constexpr uint32_t kWaitPolls = 1u << 26;
+constexpr uint32_t kWaitPolls = 1u << 22;          // polls with sleeps of up to 256 ns: about 1 s
+constexpr int kXAhead = 3;                          // X rows are copied this many stages ahead
+constexpr int kXSlots = kXAhead + 1;                // slots of the X copy ring
 
 template <int PREC>
 struct SliceCfg;
@@ -90,6 +92,7 @@ struct TcArgs {
   int k;
   uint64_t seed;
   uint32_t stream_id;
+  uint32_t rk[20];    // Philox round keys of the seed (see philox4x32_10_keys)
   int64_t row_offset;
   int64_t blk0;       // first 1024-row block (global index)
   int64_t nblk;       // blocks covering [row_offset, row_offset + m)
@@ -97,6 +100,7 @@ struct TcArgs {
   int ngrp;           // column groups
   int D;              // pipeline stages
   int vec;            // X rows may be read 16 bytes at a time
+  const int *eblk;    // column exponents of the blocks: eblk[(blk - blk0) * n + j]
   double *partial;    // [groups][n][k]
   long long *acc64;   // int64 accumulators, KCH * NC * 128 per CTA
   int *status;        // nullable
@@ -124,6 +128,21 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Packed pairs (add.rn.f32x2 / mul.rn.f32x2 of the sm_100 family): two
+// independent IEEE round-to-nearest operations in one instruction.
+__device__ __forceinline__ void add2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
 
 // 8 consecutive rows lr0 .. lr0+7 of column j (zeros outside X).
 template <class T>
@@ -203,32 +222,37 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
     }
   } else {
     // FP32 / BF16 storage: t = x 2^(6-e); digit b = t rounded to a multiple of
-    // 2^(-7b) by adding and removing 1.5 2^(23-7b); t -= digit (both exact)
+    // 2^(-7b) by adding and removing 1.5 2^(23-7b); t -= digit (both exact).
+    // Pairs of rows go through the packed f32x2 unit.
     float t8[8];
     const int sh = 6 - e;
-    const float s1 = pow2f(sh / 2), s2 = pow2f(sh - sh / 2);
+    const bool empty = e == EMPTY_EXP;
+    const float s1 = empty ? 0.0f : pow2f(sh / 2), s2 = empty ? 0.0f : pow2f(sh - sh / 2);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      float xv;
-      if constexpr (PREC == RCQR_BF16)
-        xv = __bfloat162float(x[t]);
-      else
-        xv = x[t];
-      if (e == EMPTY_EXP || mag_bits(xv) < 0x00800000u) xv = 0.0f;
-      t8[t] = (xv * s1) * s2;
+    for (int p = 0; p < 4; ++p) {
+      float x0, x1;
+      if constexpr (PREC == RCQR_BF16) {
+        x0 = __bfloat162float(x[2 * p]);
+        x1 = __bfloat162float(x[2 * p + 1]);
+      } else {
+        x0 = x[2 * p];
+        x1 = x[2 * p + 1];
+      }
+      mul2(x0, x1, x0, x1, s1, s1);
+      mul2(t8[2 * p], t8[2 * p + 1], x0, x1, s2, s2);
     }
 #pragma unroll
     for (int b = 0; b < S; ++b) {
       const float M = __uint_as_float(((uint32_t)(150 - 7 * b) << 23) | 0x400000u);   // 1.5 2^(23-7b)
-      float d[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        d[t] = __fadd_rn(__fadd_rn(t8[t], M), -M);
-        if (b + 1 < S) t8[t] = __fadd_rn(t8[t], -d[t]);
-      }
       uint32_t w[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) w[p] = __byte_perm(__float_as_uint(d[2 * p]), __float_as_uint(d[2 * p + 1]), 0x7632);
+      for (int p = 0; p < 4; ++p) {
+        float u0, u1, d0, d1;
+        add2(u0, u1, t8[2 * p], t8[2 * p + 1], M, M);
+        add2(d0, d1, u0, u1, -M, -M);
+        if (b + 1 < S) add2(t8[2 * p], t8[2 * p + 1], t8[2 * p], t8[2 * p + 1], -d0, -d1);
+        w[p] = __byte_perm(__float_as_uint(d0), __float_as_uint(d1), 0x7632);
+      }
       *reinterpret_cast<uint4 *>(dst + b * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -248,7 +272,8 @@ __device__ __forceinline__ void theta_tile(unsigned char *sA, const uint32_t *ta
     const int i = (kgi * KCH + c) * 128 + il;
     uint32_t wv[8];
     if (i < a.k) {
-      const uint4 w = theta_block((uint64_t)(r0 / 16 + qq), (uint32_t)i, a.stream_id, a.seed);
+      const uint64_t q = (uint64_t)(r0 / 16 + qq);
+      const uint4 w = philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)i, a.stream_id), a.rk);
       const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int p = 0; p < 8; ++p) {
@@ -267,13 +292,17 @@ __device__ __forceinline__ void theta_tile(unsigned char *sA, const uint32_t *ta
   }
 }
 
-// Bounded mbarrier wait that gives up at once when another thread of the CTA
-// has already timed out (so one failure costs one timeout, not one per stage).
-__device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int *fail) {
+// Bounded mbarrier wait with growing sleeps between polls (a waiting warp
+// leaves the issue slots to the working ones); gives up at once when another
+// thread of the CTA has already timed out.
+__device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int *fail, uint32_t max_sleep_ns) {
   volatile int *f = fail;
-  for (uint32_t round = 0; round < (kWaitPolls >> 10); ++round) {
+  uint32_t ns = 16;
+  for (uint32_t round = 0; round < kWaitPolls; ++round) {
+    if (umma::mbar_wait(bar, parity, 1)) return;
     if (*f) return;
-    if (umma::mbar_wait(bar, parity, 1024)) return;
+    __nanosleep(ns);
+    ns = ns * 2 < max_sleep_ns ? ns * 2 : max_sleep_ns;
   }
   *f = 1;
 }
@@ -310,10 +339,10 @@ struct Tc {
   };
 
   // Folds block b's TMEM accumulators into the int64 accumulators (all threads).
-  static __device__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc, const TcArgs &a, int kgi,
+  static __device__ __noinline__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc, const TcArgs &a, int kgi,
                               int col0, int g) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail);
+    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256);
     umma::fence_after_sync();
     const bool last = b == NB - 1;
     const int p = b & 1;
@@ -324,6 +353,13 @@ struct Tc {
       for (int jc0 = 0; jc0 < CW; jc0 += 8) {
 #pragma unroll
         for (int c = 0; c < KCH; ++c) {
+          // this thread's 8 accumulators of the chunk are contiguous: Acc[(c 128 + il) NC + jl]
+          longlong2 *ap = reinterpret_cast<longlong2 *>(Acc + ((size_t)c * 128 + il) * NC + cq * CW + jc0);
+          longlong2 old2[4];
+          if (b > 0) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) old2[h] = ap[h];
+          }
           uint32_t rv[NACC][8];
 #pragma unroll
           for (int acc = 0; acc < NACC; ++acc)
@@ -331,18 +367,18 @@ struct Tc {
                            rv[acc]);
           umma::tmem_wait_ld();
           const int i = (kgi * KCH + c) * 128 + il;
+          long long out[8];
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int jl = cq * CW + jc0 + jj;
             const int e = sh.e_col[p][jl];
             const int Ec = sh.E_col[p][jl];
-            long long *ap = Acc + ((size_t)c * NC + jl) * 128 + il;
+            const long long old = b > 0 ? ((jj & 1) ? old2[jj >> 1].y : old2[jj >> 1].x) : 0LL;
             long long acc_v;
             int En;
             if (e == EMPTY_EXP) {
-              if (!last) continue;
               En = Ec;
-              acc_v = Ec == EMPTY_EXP ? 0LL : *ap;
+              acc_v = Ec == EMPTY_EXP ? 0LL : old;
             } else {
               long long V = 0;
 #pragma unroll
@@ -355,22 +391,24 @@ struct Tc {
                 En = f;
               } else if (f >= Ec) {
                 const int s = f - Ec;
-                const long long old = *ap;
                 acc_v = (s >= 63 ? (old < 0 ? -1LL : 0LL) : (old >> s)) + V;
                 En = f;
               } else {
                 const int s = Ec - f;
-                acc_v = *ap + (s >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> s));
+                acc_v = old + (s >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> s));
                 En = Ec;
               }
             }
+            out[jj] = acc_v;
             if (last) {
               const int j = col0 + jl;
               if (i < a.k && j < a.n)
                 a.partial[((int64_t)g * a.n + j) * a.k + i] = En == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, En);
-            } else {
-              *ap = acc_v;
             }
+          }
+          if (!last) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) ap[h] = make_longlong2(out[2 * h], out[2 * h + 1]);
           }
         }
       }
@@ -390,12 +428,49 @@ struct Tc {
   }
 };
 
+// Asynchronous 16-byte global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(umma::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Column exponents of every 1024-row block: eblk[(blk - blk0) * n + j].  One
+// warp per (block, column), 8 per CTA; the rows outside [0, m) are skipped.
+template <class T>
+__global__ void __launch_bounds__(256) block_exp_kernel(const T *__restrict__ X, int64_t m, int n, int64_t ldx,
+                                                        int64_t row_offset, int64_t blk0, int64_t nblk,
+                                                        int *__restrict__ eblk) {
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= nblk * n) return;
+  const int64_t bl = w / n;
+  const int j = (int)(w % n);
+  const int64_t lr0 = (blk0 + bl) * kBlockRows - row_offset;
+  const T *col = X + (int64_t)j * ldx;
+  decltype(mag_bits(T(0))) mx = 0;
+  for (int r = lane; r < kBlockRows; r += 32) {
+    const int64_t lr = lr0 + r;
+    if (lr >= 0 && lr < m) mx = max(mx, mag_bits(__ldg(col + lr)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) eblk[w] = block_exp(mx);
+}
+
 template <int PREC, int KCH, int JCH>
 __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   using K = Tc<PREC, KCH, JCH>;
   using T = typename K::T;
-  using MaxT = typename K::MaxT;
   constexpr int NC = K::NC, S = K::S;
+  constexpr int NTASK = 4 * NC;                        // (column, 8-row octet) pairs per stage
+  constexpr int NXT = 32 * kXWarps;
+  constexpr int TPT = (NTASK + NXT - 1) / NXT;         // tasks per X thread (the last ones partial)
+  constexpr int H = (int)(8 * sizeof(T) / 16);         // 16-byte chunks per octet
+  constexpr int SLOT_BYTES = NTASK * 8 * (int)sizeof(T);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ typename K::Shared sh;
 
@@ -406,13 +481,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   const int col0 = ngi * NC;
   const T *X = static_cast<const T *>(a.X);
   uint32_t *table = reinterpret_cast<uint32_t *>(smem_raw);
-  unsigned char *stage_base = smem_raw + kTableBytes;
+  unsigned char *xring = smem_raw + kTableBytes;
+  unsigned char *stage_base = xring + kXSlots * SLOT_BYTES;
+
+  const int64_t bb = a.blk0 + (a.nblk * g) / a.groups;
+  const int64_t be_ = a.blk0 + (a.nblk * (g + 1)) / a.groups;
+  const int NB = (int)(be_ - bb);
+  const int total = NB * kSPB;
+  long long *Acc = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (KCH * NC * 128);
 
   for (int e = tid; e < 256 * 32; e += kThreadsTC) {
     const int lev = (int)c_theta_levels[e >> 5];
     table[e] = __float_as_uint((float)lev) >> 16;
   }
-  for (int j = tid; j < NC; j += kThreadsTC) sh.E_col[0][j] = EMPTY_EXP;
+  for (int j = tid; j < NC; j += kThreadsTC) {
+    sh.E_col[0][j] = EMPTY_EXP;
+    sh.e_col[0][j] = col0 + j < a.n ? a.eblk[(bb - a.blk0) * a.n + col0 + j] : EMPTY_EXP;
+  }
   if (tid == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       umma::mbar_init(&sh.full[s], kProdWarps);
@@ -422,42 +507,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     sh.s_fail = 0;
   }
   if (warp == 0) umma::tmem_alloc(&sh.tslot, K::NCOLS);
-
-  const int64_t bb = a.blk0 + (a.nblk * g) / a.groups;
-  const int64_t be_ = a.blk0 + (a.nblk * (g + 1)) / a.groups;
-  const int NB = (int)(be_ - bb);
-  const int total = NB * kSPB;
-  long long *Acc = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (KCH * NC * 128);
-
-  // X warps: this thread's columns and 8-row octet within a stage
-  const bool is_x = warp >= kThetaWarps && warp < kProdWarps;
-  const int xw = warp - kThetaWarps;
-  const int oc = lane >> 3;
-  int jl_u[JCH];
-#pragma unroll
-  for (int u = 0; u < JCH; ++u) jl_u[u] = 64 * u + 8 * xw + (lane & 7);
-
-  // exponents of the first block
-  if (is_x) {
-    MaxT mx[JCH];
-#pragma unroll
-    for (int u = 0; u < JCH; ++u) mx[u] = 0;
-    for (int st = 0; st < kSPB; ++st) {
-#pragma unroll
-      for (int u = 0; u < JCH; ++u) {
-        T v[8];
-        load8<T>(X, bb * kBlockRows + st * kBK + 8 * oc - a.row_offset, col0 + jl_u[u], a, v);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) mx[u] = max(mx[u], mag_bits(v[t]));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < JCH; ++u) {
-      mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 8));
-      mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 16));
-      if (oc == 0) sh.e_col[0][jl_u[u]] = col0 + jl_u[u] < a.n ? block_exp(mx[u]) : EMPTY_EXP;
-    }
-  }
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -469,7 +518,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     int next = 0;
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail);
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
       const int b = it / kSPB, st = it % kSPB;
       theta_tile<KCH>(stage_base + slot * K::STAGE_BYTES, tabp, tid, (bb + b) * kBlockRows + st * kBK, kgi, a);
       umma::fence_proxy_async();
@@ -477,88 +526,124 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
       if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
     }
-  } else if (is_x) {
-    // ---- X producers
-    T cur[JCH][8], nxt[JCH][8];
-    MaxT mx[JCH];
+  } else if (warp < kProdWarps) {
+    // ---- X producers: task o = xt + NXT u is column jl = 8 (o / 32) + o % 8, octet oc = (o / 8) % 4
+    // (8 consecutive lanes: 8 consecutive columns of one octet, so the slice stores do not conflict)
+    const int xt = tid - 32 * kThetaWarps;
+    // copies the octet of task o for stage s into ring slot `slot` (asynchronously where possible)
+    auto issue = [&](int s, int slot, int o) {
+      const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
+      const int j = col0 + jl;
+      const int64_t lr0 = (bb + s / kSPB) * kBlockRows + (s % kSPB) * kBK + 8 * oc - a.row_offset;
+      unsigned char *dst = xring + slot * SLOT_BYTES + o * 16;
+      if (j < a.n && a.vec && lr0 >= 0 && lr0 + 8 <= a.m) {
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(X + lr0 + (int64_t)j * a.ldx);
 #pragma unroll
-    for (int u = 0; u < JCH; ++u) {
-      mx[u] = 0;
-      load8<T>(X, bb * kBlockRows + 8 * oc - a.row_offset, col0 + jl_u[u], a, cur[u]);
+        for (int h = 0; h < H; ++h) cp_async16(dst + h * (NTASK * 16), src + 16 * h);
+      } else {
+        __align__(16) T v[8];
+        load8<T>(X, lr0, j, a, v);
+#pragma unroll
+        for (int h = 0; h < H; ++h) *reinterpret_cast<uint4 *>(dst + h * (NTASK * 16)) = reinterpret_cast<const uint4 *>(v)[h];
+      }
+    };
+#pragma unroll 1
+    for (int s = 0; s < kXAhead; ++s) {
+      if (s < total)
+#pragma unroll
+        for (int u = 0; u < TPT; ++u)
+          if (xt + NXT * u < NTASK) issue(s, s % kXSlots, xt + NXT * u);
+      cp_async_commit();
+    }
+    int e_cur[TPT], e_nxt[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int o = xt + NXT * u;
+      const int jl = 8 * (o >> 5) + (o & 7);
+      e_cur[u] = (o < NTASK && col0 + jl < a.n) ? a.eblk[(bb - a.blk0) * a.n + col0 + jl] : EMPTY_EXP;
+      e_nxt[u] = e_cur[u];
     }
     int next = 0;
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       const int b = it / kSPB, st = it % kSPB;
-      const int64_t r0 = (bb + b) * kBlockRows + st * kBK;
-      const bool more_blocks = b + 1 < NB;
-      if (it + 1 < total) {
-        const int64_t r1 = (bb + (it + 1) / kSPB) * kBlockRows + ((it + 1) % kSPB) * kBK;
+      if (it + kXAhead < total)
 #pragma unroll
-        for (int u = 0; u < JCH; ++u) load8<T>(X, r1 + 8 * oc - a.row_offset, col0 + jl_u[u], a, nxt[u]);
-      }
-      T ex[JCH][8];
-      if (more_blocks) {
+        for (int u = 0; u < TPT; ++u)
+          if (xt + NXT * u < NTASK) issue(it + kXAhead, (it + kXAhead) % kXSlots, xt + NXT * u);
+      cp_async_commit();
+      if (st == kSPB / 2 && b + 1 < NB) {
+        // exponents of the next block, read early
 #pragma unroll
-        for (int u = 0; u < JCH; ++u) load8<T>(X, r0 + kBlockRows + 8 * oc - a.row_offset, col0 + jl_u[u], a, ex[u]);
+        for (int u = 0; u < TPT; ++u) {
+          const int o = xt + NXT * u;
+          const int jl = 8 * (o >> 5) + (o & 7);
+          e_nxt[u] = (o < NTASK && col0 + jl < a.n) ? a.eblk[(bb - a.blk0 + b + 1) * a.n + col0 + jl] : EMPTY_EXP;
+        }
       }
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail);
+      if (st == 0 && b > 0) {
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+          const int o = xt + NXT * u;
+          e_cur[u] = e_nxt[u];
+          if (o < NTASK && ((o >> 3) & 3) == 0) sh.e_col[b & 1][8 * (o >> 5) + (o & 7)] = e_cur[u];
+        }
+      }
+      cp_async_wait<kXAhead>();
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
       unsigned char *sB = stage_base + slot * K::STAGE_BYTES + K::A_BYTES;
-      const int p = b & 1;
+      const unsigned char *src = xring + (it % kXSlots) * SLOT_BYTES;
 #pragma unroll
-      for (int u = 0; u < JCH; ++u) {
-        const int jl = jl_u[u];
-        slice8_store<PREC>(cur[u], sh.e_col[p][jl], sB + (jl >> 3) * (kBK * 16) + oc * 128 + (jl & 7) * 16,
-                           NC * kBK * 2);
+      for (int u = 0; u < TPT; ++u) {
+        const int o = xt + NXT * u;
+        if (o < NTASK) {
+          const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
+          __align__(16) T v[8];
+#pragma unroll
+          for (int h = 0; h < H; ++h)
+            reinterpret_cast<uint4 *>(v)[h] = *reinterpret_cast<const uint4 *>(src + h * (NTASK * 16) + o * 16);
+          slice8_store<PREC>(v, e_cur[u], sB + (jl >> 3) * (kBK * 16) + oc * 128 + (jl & 7) * 16, NC * kBK * 2);
+        }
       }
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
-      if (more_blocks) {
-#pragma unroll
-        for (int u = 0; u < JCH; ++u)
-#pragma unroll
-          for (int t = 0; t < 8; ++t) mx[u] = max(mx[u], mag_bits(ex[u][t]));
-        if (st == kSPB - 1) {
-#pragma unroll
-          for (int u = 0; u < JCH; ++u) {
-            mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 8));
-            mx[u] = max(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], 16));
-            if (oc == 0) sh.e_col[p ^ 1][jl_u[u]] = col0 + jl_u[u] < a.n ? block_exp(mx[u]) : EMPTY_EXP;
-            mx[u] = 0;
-          }
-          __syncwarp();
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < JCH; ++u)
-#pragma unroll
-        for (int t = 0; t < 8; ++t) cur[u][t] = nxt[u][t];
       if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
     }
+    cp_async_wait<0>();
   } else {
     // ---- MMA warp: one thread issues, the warp folds with the others
-    const uint32_t idesc = umma::idesc_bf16_f32(128, NC);
+    // Slices 0..NE feed consecutive accumulators and sit consecutively in the
+    // stage, so up to 256 / NC of them form one MMA with N = (count) NC (the
+    // Theta tile is then read once for all of them); the slices below NE add
+    // into accumulator NE one MMA each.
+    constexpr int G = 256 / NC;
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       const int b = it / kSPB, st = it % kSPB;
       if (lane == 0) {
-        wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail);
+        wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail, 64);
         umma::fence_after_sync();
         const uint32_t a0 = umma::smem_u32(stage_base + slot * K::STAGE_BYTES);
         const uint32_t b0 = a0 + K::A_BYTES;
 #pragma unroll
         for (int c = 0; c < KCH; ++c)
 #pragma unroll
-          for (int bs = 0; bs < S; ++bs) {
-            const int acc = bs < K::NE ? bs : K::NE;
-            const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + acc) * NC);
+          for (int q = 0; q < kBK / 16; ++q) {
+            const uint64_t ad = umma::smem_desc(a0 + c * (128 * kBK * 2) + q * 256, 128, kBK * 16);
+            const bool first = (st == 0) && (q == 0);
 #pragma unroll
-            for (int q = 0; q < kBK / 16; ++q) {
-              const uint64_t ad = umma::smem_desc(a0 + c * (128 * kBK * 2) + q * 256, 128, kBK * 16);
+            for (int g0 = 0; g0 <= K::NE; g0 += G) {
+              const int cnt = (K::NE + 1 - g0) < G ? (K::NE + 1 - g0) : G;
+              const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + g0) * NC);
+              const uint64_t bd = umma::smem_desc(b0 + g0 * (NC * kBK * 2) + q * 256, 128, kBK * 16);
+              umma::mma_bf16(dcol, ad, bd, umma::idesc_bf16_f32(128, cnt * NC), first ? 0u : 1u);
+            }
+#pragma unroll
+            for (int bs = K::NE + 1; bs < S; ++bs) {
+              const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + K::NE) * NC);
               const uint64_t bd = umma::smem_desc(b0 + bs * (NC * kBK * 2) + q * 256, 128, kBK * 16);
-              const bool first = (st == 0) && (q == 0) && (bs <= K::NE);
-              umma::mma_bf16(dcol, ad, bd, idesc, first ? 0u : 1u);
+              umma::mma_bf16(dcol, ad, bd, umma::idesc_bf16_f32(128, NC), 1u);
             }
           }
         umma::mma_commit(&sh.empty[slot]);
@@ -617,11 +702,12 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   const int kchunks = (int)((k + 127) / 128);
   p.KCH = (p.JCH == 1 && kchunks >= 2 && 2 * nacc * 64 <= 512) ? 2 : 1;
   p.kgrp = (kchunks + p.KCH - 1) / p.KCH;
-  // as many 32-row stages as fit beside the level table (at most kMaxStages)
+  // as many 32-row stages as fit beside the level table and the X copy ring (at most kMaxStages)
   const size_t stage = (size_t)p.KCH * 128 * kBK * 2 + (size_t)p.S * p.NC * kBK * 2;
-  const size_t budget = 220 * 1024 - kTableBytes;
+  const size_t ring = (size_t)kXSlots * 4 * p.NC * 8 * elem_size(prec);
+  const size_t budget = 220 * 1024 - kTableBytes - ring;
   p.D = (int)std::min<size_t>(kMaxStages, budget / stage);
-  p.smem = kTableBytes + (size_t)p.D * stage;
+  p.smem = kTableBytes + ring + (size_t)p.D * stage;
   p.blk0 = row_offset / kBlockRows;
   p.nblk = (row_offset + m + kBlockRows - 1) / kBlockRows - p.blk0;
   const int64_t ctas_per_rows = (int64_t)p.kgrp * p.ngrp;
@@ -668,6 +754,7 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, 
   Workspace w(nullptr, 0);
   w.take<double>((size_t)p.groups * n * k);
   w.take<long long>(acc64_count(p));
+  w.take<int>((size_t)p.nblk * n);
   return w.used;
 }
 
@@ -685,7 +772,8 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   const TcPlan p = plan_tc(m, n, k, row_offset, prec);
   double *partial = ws.take<double>((size_t)p.groups * n * k);
   long long *acc64 = ws.take<long long>(acc64_count(p));
-  if (!partial || !acc64) return cudaErrorMemoryAllocation;
+  int *eblk = ws.take<int>((size_t)p.nblk * n);
+  if (!partial || !acc64 || !eblk) return cudaErrorMemoryAllocation;
   TcArgs a;
   a.X = X;
   a.m = m;
@@ -694,6 +782,10 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   a.k = (int)k;
   a.seed = seed;
   a.stream_id = stream_id;
+  for (int r = 0; r < 10; ++r) {
+    a.rk[2 * r] = (uint32_t)seed + (uint32_t)r * 0x9E3779B9u;
+    a.rk[2 * r + 1] = (uint32_t)(seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+  }
   a.row_offset = row_offset;
   a.blk0 = p.blk0;
   a.nblk = p.nblk;
@@ -704,9 +796,24 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   a.vec = ((uintptr_t)X % 16 == 0) && ((size_t)ldx * es) % 16 == 0 && ((size_t)row_offset * es) % 16 == 0;
   a.partial = partial;
   a.acc64 = acc64;
+  a.eblk = eblk;
   a.status = dev_status;
   dim3 grid((unsigned)(p.kgrp * p.ngrp), (unsigned)p.groups);
   cudaError_t e;
+  {
+    const unsigned eg = (unsigned)((p.nblk * n + 7) / 8);
+    switch (prec) {
+      case RCQR_F64:
+        block_exp_kernel<double><<<eg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk, eblk);
+        break;
+      case RCQR_F32:
+        block_exp_kernel<float><<<eg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk, eblk);
+        break;
+      default:
+        block_exp_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n, ldx, row_offset,
+                                                            p.blk0, p.nblk, eblk);
+    }
+  }
   switch (prec) {
     case RCQR_F64: e = launch_tc_prec<RCQR_F64>(a, p, grid, st); break;
     case RCQR_F32: e = launch_tc_prec<RCQR_F32>(a, p, grid, st); break;

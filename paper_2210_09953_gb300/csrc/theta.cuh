@@ -24,6 +24,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same ten rounds with the round keys given: rk[2r] = k0 + r W0 and
+// rk[2r+1] = k1 + r W1 (mod 2^32), r = 0..9, e.g. as kernel parameters, so that
+// no key arithmetic runs per call.
+__device__ __forceinline__ uint4 philox4x32_10_keys(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * round], lo1, hi0 ^ c.w ^ rk[2 * round + 1], lo0);
+  }
+  return c;
+}
+
 // The 16 bytes of Theta's row i for the 16-row block q (global rows 16q..16q+15).
 __device__ __forceinline__ uint4 theta_block(uint64_t q, uint32_t i, uint32_t stream, uint64_t seed) {
   return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), i, stream), (uint32_t)seed,
