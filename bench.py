@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -26,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 M, N, K, COND = 4194304, 64, 256, 1e8
 SEED_X, SEED_THETA = 1002, 0x5EED0002
-ORACLE_ROWS = 1 << 19          # bounded sample for the CPU oracle (about 10-30 s of work)
+ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (about 10-20 s on 16 cores)
 
 
 def parse():
@@ -98,7 +99,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"rcqr_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -261,9 +262,10 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sketch_bytes = m * N * 4                 # algorithmic: X read once
     achieved = sketch_bytes / (ms_sketch * 1e-3) / 1e9
-    # per factorization (mixed path, Alg. 3): status reset, sketch + its reduction, TSQR leaves + fold,
-    # rank, TRSM prep + rows, Gram + reduction, Cholesky update, TRSM prep + rows
-    launches_per_step = 13
+    # per factorization (mixed path, Alg. 3): status reset, sketch (block exponents, tensor-core
+    # sketch, reduction), TSQR leaves + fold, rank, TRSM prep + rows, Gram + reduction,
+    # Cholesky update, TRSM prep + rows
+    launches_per_step = 14
 
     if rank == 0:
         cpu = None
