@@ -37,17 +37,20 @@ __device__ __forceinline__ double warp0_sum(double v) {
 }
 
 // Dot products for the column updates: four threads per column, each summing
-// every fourth row with two accumulators, the quarter sums combined by two
+// every fourth row with four accumulators, the quarter sums combined by two
 // shuffles (fixed order).  Returns the full sum in all four threads.
 __device__ __forceinline__ double quad_dot(const double *a, const double *b, int i0, int i1, int q) {
-  double s0 = 0.0, s1 = 0.0;
+  // four accumulators: FP64 latency, not throughput, bounds these short sums
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int i = i0 + q;
-  for (; i + 4 < i1; i += 8) {
+  for (; i + 12 < i1; i += 16) {
     s0 = fma(a[i], b[i], s0);
     s1 = fma(a[i + 4], b[i + 4], s1);
+    s2 = fma(a[i + 8], b[i + 8], s2);
+    s3 = fma(a[i + 12], b[i + 12], s3);
   }
-  if (i < i1) s0 = fma(a[i], b[i], s0);
-  double s = s0 + s1;
+  for (; i < i1; i += 4) s0 = fma(a[i], b[i], s0);
+  double s = (s0 + s1) + (s2 + s3);
   s += __shfl_xor_sync(0xffffffffu, s, 1);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
   return s;
@@ -60,9 +63,14 @@ __device__ void householder_step(double *A, int rows, int n, int lda, int j, dou
                                  double *s_diag) {
   double *col = A + (int64_t)j * lda;
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < rows; i += 32) t = fma(col[i], col[i], t);
-    t = warp0_sum(t);
+    double t = 0.0, t1 = 0.0;
+    int i = j + 1 + threadIdx.x;
+    for (; i + 32 < rows; i += 64) {
+      t = fma(col[i], col[i], t);
+      t1 = fma(col[i + 32], col[i + 32], t1);
+    }
+    if (i < rows) t = fma(col[i], col[i], t);
+    t = warp0_sum(t + t1);
     if (threadIdx.x == 0) {
       const double x0 = col[j];
       const double sigma = fma(x0, x0, t);
@@ -188,17 +196,17 @@ tsqr_leaf_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, int L,
   }
 }
 
-// T <- R of [T; B] for upper triangular n x n T and B (ld n, column-major).
-// The reflector of column j acts on row j of T and rows 0..j of B only.
-__device__ void fold_triangles(double *T, double *B, int n, double *scal) {
+// T <- R of [T; B] for upper triangular n x n T and B (column-major, leading
+// dimension ld).  The reflector of column j acts on row j of T and rows 0..j of B only.
+__device__ void fold_triangles(double *T, double *B, int n, int ld, double *scal) {
   for (int j = 0; j < n; ++j) {
-    double *bj = B + (int64_t)j * n;
+    double *bj = B + (int64_t)j * ld;
     if (threadIdx.x < 32) {
       double t = 0.0;
       for (int i = threadIdx.x; i <= j; i += 32) t = fma(bj[i], bj[i], t);
       t = warp0_sum(t);
       if (threadIdx.x == 0) {
-        const double x0 = T[j + (int64_t)j * n];
+        const double x0 = T[j + (int64_t)j * ld];
         double beta = 0.0, v0 = 0.0, d = x0;
         if (t > 0.0) {
           const double alpha = sqrt(fma(x0, x0, t));
@@ -219,32 +227,47 @@ __device__ void fold_triangles(double *T, double *B, int n, double *scal) {
       for (int c0 = j + 1; c0 < n; c0 += nq) {
         const int c = c0 + (threadIdx.x >> 2);
         const bool valid = c < n;
-        double *bc = B + (int64_t)(valid ? c : j) * n;
-        const double tjc = valid ? T[j + (int64_t)c * n] : 0.0;
+        double *bc = B + (int64_t)(valid ? c : j) * ld;
+        const double tjc = valid ? T[j + (int64_t)c * ld] : 0.0;
         const double w = fma(v0, tjc, quad_dot(bj, bc, 0, valid ? j + 1 : 0, q));
         if (valid) {
           const double bw = beta * w;
           for (int i = q; i <= j; i += 4) bc[i] = fma(-bw, bj[i], bc[i]);
-          if (q == 0) T[j + (int64_t)c * n] = fma(-bw, v0, tjc);
+          if (q == 0) T[j + (int64_t)c * ld] = fma(-bw, v0, tjc);
         }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) T[j + (int64_t)j * n] = scal[2];
+    if (threadIdx.x == 0) T[j + (int64_t)j * ld] = scal[2];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) bj[i] = 0.0;
     __syncthreads();
   }
 }
 
+// Folds the L leaf triangles into one.  The triangles are staged in shared
+// memory (odd leading dimension, conflict-free column-per-quad access) when
+// they fit, so the n sequential steps of each fold run on shared memory rather
+// than L2; otherwise they are folded in place in the workspace.
 __global__ void __launch_bounds__(kSmallThreads)
-tsqr_fold_kernel(double *Rleaf, int n, int L, double *R, int64_t ldr) {
+tsqr_fold_kernel(double *Rleaf, int n, int L, double *R, int64_t ldr, int use_smem) {
+  extern __shared__ double smem[];
   __shared__ double scal[4];
-  for (int l = 1; l < L; ++l) fold_triangles(Rleaf, Rleaf + (int64_t)l * n * n, n, scal);
+  const int ld = use_smem ? (n | 1) : n;
+  double *W = use_smem ? smem : Rleaf;
+  if (use_smem) {
+    for (int64_t e = threadIdx.x; e < (int64_t)L * n * n; e += blockDim.x) {
+      const int l = (int)(e / ((int64_t)n * n)), rem = (int)(e % ((int64_t)n * n));
+      const int i = rem % n, c = rem / n;
+      W[(int64_t)l * n * ld + i + (int64_t)c * ld] = Rleaf[e];
+    }
+    __syncthreads();
+  }
+  for (int l = 1; l < L; ++l) fold_triangles(W, W + (int64_t)l * n * ld, n, ld, scal);
   __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e % n, c = e / n;
-    const double sg = Rleaf[i + (int64_t)i * n] < 0.0 ? -1.0 : 1.0;
-    R[i + (int64_t)c * ldr] = i <= c ? sg * Rleaf[i + (int64_t)c * n] : 0.0;
+    const double sg = W[i + (int64_t)i * ld] < 0.0 ? -1.0 : 1.0;
+    R[i + (int64_t)c * ldr] = i <= c ? sg * W[i + (int64_t)c * ld] : 0.0;
   }
 }
 
@@ -488,7 +511,14 @@ __global__ void set_rank_kernel(int64_t *rank, int64_t v) { *rank = v; }
 size_t copy_bytes(int64_t rows, int64_t n) { return (size_t)((rows | 1) * n) * 8; }
 bool fits_smem(int64_t rows, int64_t n) { return copy_bytes(rows, n) <= kSmemLimit; }
 
-int tsqr_leaves(int64_t k, int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(k / n, 32)); }
+// Leaves of the TSQR tree.  Every Householder step is a chain of dependent FP64
+// operations (a reduction, a square root, a division) of a few microseconds on
+// GB300, and a tree of L leaves costs n steps per leaf level plus n per fold,
+// so the sketch is split only when it is much taller than 4n.
+int tsqr_leaves(int64_t k, int64_t n) {
+  if (k <= 4 * n) return 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(k / (4 * n), 32));
+}
 
 }  // namespace
 
@@ -511,7 +541,10 @@ cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, d
   const size_t bytes = sm ? copy_bytes(rows_max, n) : 0;
   if (sm) set_smem(tsqr_leaf_kernel, (int)kSmemLimit);
   tsqr_leaf_kernel<<<L, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, L, Rleaf, g, sm);
-  tsqr_fold_kernel<<<1, kSmallThreads, 0, st>>>(Rleaf, (int)n, L, R, ldr);
+  const size_t fold_bytes = (size_t)L * n * (n | 1) * 8;
+  const bool fold_sm = fold_bytes <= kSmemLimit;
+  if (fold_sm) set_smem(tsqr_fold_kernel, (int)kSmemLimit);
+  tsqr_fold_kernel<<<1, kSmallThreads, fold_sm ? fold_bytes : 0, st>>>(Rleaf, (int)n, L, R, ldr, fold_sm);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,10 @@ __global__ void trsm32_prep_kernel(const double *__restrict__ R, int n, int64_t 
     dinv[j] = j < r ? __double2float_rn(1.0 / R[j + (int64_t)j * ldr]) : 0.0f;
 }
 
-template <class TX, int NB>
+// RR rows per thread (RR = 2 for NB <= 64): every R value read from shared
+// memory (a broadcast) serves RR rows, so the shared-memory traffic per FMA is
+// 1 / RR of the one-row form.  Rows row0 + t * kT32Threads, t < RR.
+template <class TX, int NB, int RR>
 __global__ void __launch_bounds__(kT32Threads)
 trsm32_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const float *__restrict__ Rf,
               const float *__restrict__ dinv, const int32_t *__restrict__ perm,
@@ -52,54 +55,80 @@ trsm32_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const flo
   for (int j = threadIdx.x; j < NB; j += blockDim.x) Ds[j] = dinv[j];
   __syncthreads();
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= m) return;
-  float q[NB];
+  const int64_t row0 = (int64_t)blockIdx.x * (RR * kT32Threads) + threadIdx.x;
+  if (row0 >= m) return;
+  bool live[RR];
+#pragma unroll
+  for (int t = 0; t < RR; ++t) live[t] = row0 + (int64_t)t * kT32Threads < m;
+  float q[RR][NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
-    float v = 0.0f;
-    if (j < r) {
-      const int src = perm ? perm[j] : j;
-      v = to_f32(X[row + (int64_t)src * ldx]);
-    }
-    q[j] = v;
+    const int src = (perm && j < r) ? perm[j] : j;
+#pragma unroll
+    for (int t = 0; t < RR; ++t)
+      q[t][j] = (j < r && live[t]) ? to_f32(X[row0 + (int64_t)t * kT32Threads + (int64_t)src * ldx]) : 0.0f;
   }
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     const float *rc = Rs + j * NB;
-    float s = q[j];
+    float s[RR];
+#pragma unroll
+    for (int t = 0; t < RR; ++t) s[t] = q[t][j];
 #pragma unroll
     for (int i4 = 0; i4 < j / 4; ++i4) {
       const float4 rv = *reinterpret_cast<const float4 *>(rc + 4 * i4);
-      s = fmaf(-q[4 * i4 + 0], rv.x, s);
-      s = fmaf(-q[4 * i4 + 1], rv.y, s);
-      s = fmaf(-q[4 * i4 + 2], rv.z, s);
-      s = fmaf(-q[4 * i4 + 3], rv.w, s);
+#pragma unroll
+      for (int t = 0; t < RR; ++t) {
+        s[t] = fmaf(-q[t][4 * i4 + 0], rv.x, s[t]);
+        s[t] = fmaf(-q[t][4 * i4 + 1], rv.y, s[t]);
+        s[t] = fmaf(-q[t][4 * i4 + 2], rv.z, s[t]);
+        s[t] = fmaf(-q[t][4 * i4 + 3], rv.w, s[t]);
+      }
     }
 #pragma unroll
-    for (int i = (j / 4) * 4; i < j; ++i) s = fmaf(-q[i], rc[i], s);
-    q[j] = s * Ds[j];
+    for (int i = (j / 4) * 4; i < j; ++i) {
+      const float rvi = rc[i];
+#pragma unroll
+      for (int t = 0; t < RR; ++t) s[t] = fmaf(-q[t][i], rvi, s[t]);
+    }
+    const float dj = Ds[j];
+#pragma unroll
+    for (int t = 0; t < RR; ++t) q[t][j] = s[t] * dj;
   }
 #pragma unroll
   for (int j = 0; j < NB; ++j)
-    if (j < n) Q[row + (int64_t)j * ldq] = q[j];
+    if (j < n)
+#pragma unroll
+      for (int t = 0; t < RR; ++t)
+        if (live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * ldq] = q[t][j];
 }
 
 // ---- Gram A = Q^T Q in FP32 with compensated chunk sums
 constexpr int kG32Rows = 64;     // rows per shared-memory chunk
-constexpr int kG32Stride = 65;   // column stride in shared memory (conflict-free)
+constexpr int kG32Stride = 68;   // column stride in shared memory (16-byte rows, conflict-free quads)
+
+constexpr int kG32Stages = 3;    // chunks in flight (cp.async ring)
+constexpr int kG32Slab = 64 * kG32Stride;   // floats per 64-column slab of a chunk
+
+__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
 
 // CTA (tile, g): the 64 x 64 block (bi, bj) of A, bi <= bj, from row range g.
-// 256 threads = 2 row-interleaved groups of 128; thread (ti, tj) of a group owns
-// A entries (bi*64 + ti + 16a, bj*64 + tj + 8b), a < 4, b < 8.
+// 256 threads = 2 groups of 128 that take the two 32-row halves of each
+// 64-row chunk; thread (ti, tj) of a group owns A entries
+// (bi*64 + ti + 16a, bj*64 + tj + 8b), a < 4, b < 8.  Chunks stream through a
+// ring of kG32Stages shared-memory slots (cp.async, 16 bytes = 4 rows of one
+// column per copy; `vec` = false falls back to plain loads).  Four rows of a
+// column are read at once (16-byte loads).
 __global__ void __launch_bounds__(256)
 gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const int64_t *__restrict__ rank,
-              int groups, double *__restrict__ partial, const float *__restrict__ Q2, int64_t ldq2) {
-  // two 64-column slabs of the chunk (column-major, stride 65), reused for the final reduction
-  __shared__ double smd[64 * kG32Stride];
-  float *qa = reinterpret_cast<float *>(smd);
-  float *qb = qa + 64 * kG32Stride;
-  double *red = smd;                         // 128 x 32 doubles <= 2 x 64 x 65 floats
+              int groups, double *__restrict__ partial, const float *__restrict__ Q2, int64_t ldq2, int vec) {
+  extern __shared__ float4 g32_smem4[];
+  float *ring = reinterpret_cast<float *>(g32_smem4);
+  double *red = reinterpret_cast<double *>(g32_smem4);   // 128 x 32 doubles, reused at the end
   const int nb = (n + 63) / 64;
   // Q2 == nullptr: the Gram Q^T Q, upper tiles only; else Q^T Q2, every tile
   int bi = 0, bj = 0;
@@ -126,69 +155,67 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
   const int64_t nch = (m + kG32Rows - 1) / kG32Rows;
   const int64_t cb = (nch * g) / groups, ce = (nch * (g + 1)) / groups;
   const bool diag = bi == bj && Q2 == nullptr;
-  const float *qsb = diag ? qa : qb;
+  const int slabs = diag ? 1 : 2;
   const float *Qb = Q2 ? Q2 : Q;
   const int64_t ldb = Q2 ? ldq2 : ldq;
-  // chunk loads: thread owns 4 row-quads (4 consecutive rows of one column) per slab,
-  // prefetched into registers one chunk ahead
-  float4 pa[4], pb[4];
-  auto load_chunk = [&](int64_t ch) {
+  // copies chunk ch into ring slot `slot`: (slab, column c, row quad rq) per 16 bytes
+  auto issue = [&](int64_t ch, int slot) {
     const int64_t r0 = ch * kG32Rows;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = tid + 256 * u;
-      const int c = f >> 4, rq = f & 15;
+    for (int f = tid; f < slabs * 1024; f += 256) {
+      const int sl = f >> 10, c = (f >> 4) & 63, rq = f & 15;
+      const int col = (sl == 0 ? bi : bj) * 64 + c;
+      const float *base = sl == 0 ? Q : Qb;
+      const int64_t ld = sl == 0 ? ldq : ldb;
       const int64_t row = r0 + 4 * rq;
-      const int ca = bi * 64 + c, cbb = bj * 64 + c;
-      float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
+      float *dst = ring + (slot * 2 + sl) * kG32Slab + c * kG32Stride + 4 * rq;
+      const int64_t left = m - row;
+      const int valid = (col < r && left > 0) ? (int)(left < 4 ? left : 4) : 0;
+      if (vec) {
+        const float *src = valid > 0 ? base + row + (int64_t)col * ld : base;
+        cp_async16_zfill(dst, src, 4 * valid);
+      } else {
+        float v[4];
 #pragma unroll
-      for (int k4 = 0; k4 < 4; ++k4) {
-        if (row + k4 < m) {
-          if (ca < r) va[k4] = Q[row + k4 + (int64_t)ca * ldq];
-          if (!diag && cbb < r) vb[k4] = Qb[row + k4 + (int64_t)cbb * ldb];
-        }
+        for (int k4 = 0; k4 < 4; ++k4) v[k4] = k4 < valid ? base[row + k4 + (int64_t)col * ld] : 0.0f;
+        *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
       }
-      pa[u] = make_float4(va[0], va[1], va[2], va[3]);
-      pb[u] = make_float4(vb[0], vb[1], vb[2], vb[3]);
     }
   };
-  if (cb < ce) load_chunk(cb);
+#pragma unroll 1
+  for (int s0 = 0; s0 < kG32Stages - 1; ++s0) {
+    if (cb + s0 < ce) issue(cb + s0, (int)((cb + s0) % kG32Stages));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   for (int64_t ch = cb; ch < ce; ++ch) {
+    const int64_t ahead = ch + kG32Stages - 1;
+    if (ahead < ce) issue(ahead, (int)(ahead % kG32Stages));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(kG32Stages - 1) : "memory");
     __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = tid + 256 * u;
-      const int c = f >> 4, rq = f & 15;
-      float *da = qa + c * kG32Stride + 4 * rq;
-      da[0] = pa[u].x;
-      da[1] = pa[u].y;
-      da[2] = pa[u].z;
-      da[3] = pa[u].w;
-      if (!diag) {
-        float *db = qb + c * kG32Stride + 4 * rq;
-        db[0] = pb[u].x;
-        db[1] = pb[u].y;
-        db[2] = pb[u].z;
-        db[3] = pb[u].w;
-      }
-    }
-    __syncthreads();
-    if (ch + 1 < ce) load_chunk(ch + 1);
+    const int slot = (int)(ch % kG32Stages);
+    const float *qa = ring + (slot * 2) * kG32Slab;
+    const float *qsb = diag ? qa : qa + kG32Slab;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 8; ++b) inner[a][b] = 0.0f;
-#pragma unroll 4
-    for (int rr = grp; rr < kG32Rows; rr += 2) {
-      float va[4], vb[8];
+#pragma unroll 2
+    for (int s = 0; s < 8; ++s) {
+      const int rr = 32 * grp + 4 * s;
+      float4 va[4], vb[8];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) va[a] = qa[(ti + 16 * a) * kG32Stride + rr];
+      for (int a = 0; a < 4; ++a) va[a] = *reinterpret_cast<const float4 *>(qa + (ti + 16 * a) * kG32Stride + rr);
 #pragma unroll
-      for (int b = 0; b < 8; ++b) vb[b] = qsb[(tj + 8 * b) * kG32Stride + rr];
+      for (int b = 0; b < 8; ++b) vb[b] = *reinterpret_cast<const float4 *>(qsb + (tj + 8 * b) * kG32Stride + rr);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) inner[a][b] = fmaf(va[a], vb[b], inner[a][b]);
+        for (int b = 0; b < 8; ++b) {
+          inner[a][b] = fmaf(va[a].x, vb[b].x, inner[a][b]);
+          inner[a][b] = fmaf(va[a].y, vb[b].y, inner[a][b]);
+          inner[a][b] = fmaf(va[a].z, vb[b].z, inner[a][b]);
+          inner[a][b] = fmaf(va[a].w, vb[b].w, inner[a][b]);
+        }
     }
     // Kahan: outer += inner
 #pragma unroll
@@ -200,7 +227,9 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
         comp[a][b] = (tt - outer[a][b]) - y;
         outer[a][b] = tt;
       }
+    __syncthreads();   // the slot is refilled by the next iteration's copies
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   // the two groups' sums in FP64, then this CTA's block of the partial Gram
   __syncthreads();
   if (grp == 1) {
@@ -222,18 +251,22 @@ gram32_kernel(const float *__restrict__ Q, int64_t m, int n, int64_t ldq, const 
   }
 }
 
+constexpr size_t kG32Smem = sizeof(float) * kG32Stages * 2 * kG32Slab;
+
 template <class TX>
 cudaError_t launch_trsm32_t(const TX *X, int64_t m, int64_t n, int64_t ldx, const float *Rf, const float *dinv,
                             const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq, int NB,
                             cudaStream_t st) {
-  const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);
   const size_t smem = (size_t)NB * NB * 4 + (size_t)NB * 4;
-#define RCQR_T32(NBV)                                                                                       \
-  case NBV: {                                                                                               \
-    cudaError_t e = set_smem(trsm32_kernel<TX, NBV>, (int)smem);                                           \
-    if (e != cudaSuccess) return e;                                                                         \
-    trsm32_kernel<TX, NBV><<<blocks, kT32Threads, smem, st>>>(X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq); \
-    break;                                                                                                  \
+#define RCQR_T32(NBV)                                                                                          \
+  case NBV: {                                                                                                  \
+    constexpr int RRV = NBV <= 64 ? 2 : 1;                                                                     \
+    const unsigned blocks = (unsigned)((m + RRV * kT32Threads - 1) / (RRV * kT32Threads));                      \
+    cudaError_t e = set_smem(trsm32_kernel<TX, NBV, RRV>, (int)smem);                                          \
+    if (e != cudaSuccess) return e;                                                                            \
+    trsm32_kernel<TX, NBV, RRV><<<blocks, kT32Threads, smem, st>>>(X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, \
+                                                                    ldq);                                      \
+    break;                                                                                                     \
   }
   switch (NB) {
     RCQR_T32(16)
@@ -288,7 +321,10 @@ cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, con
                           double *partial, int groups, cudaStream_t st) {
   const int64_t nb = (n + 63) / 64;
   dim3 grid((unsigned)(nb * (nb + 1) / 2), (unsigned)groups);
-  gram32_kernel<<<grid, 256, 0, st>>>(Q, m, (int)n, ldq, rank, groups, partial, nullptr, 0);
+  cudaError_t e = set_smem(gram32_kernel, (int)kG32Smem);
+  if (e != cudaSuccess) return e;
+  const int vec = ((uintptr_t)Q % 16 == 0) && (ldq % 4 == 0);
+  gram32_kernel<<<grid, 256, kG32Smem, st>>>(Q, m, (int)n, ldq, rank, groups, partial, nullptr, 0, vec);
   return cudaGetLastError();
 }
 
@@ -304,7 +340,10 @@ cudaError_t launch_cross_gram32(const float *A, int64_t lda, const float *B, int
                                 int64_t n, double *partial, int groups, cudaStream_t st) {
   const int64_t nb = (n + 63) / 64;
   dim3 grid((unsigned)(nb * nb), (unsigned)groups);
-  gram32_kernel<<<grid, 256, 0, st>>>(A, m, (int)n, lda, nullptr, groups, partial, B, ldb);
+  cudaError_t e = set_smem(gram32_kernel, (int)kG32Smem);
+  if (e != cudaSuccess) return e;
+  const int vec = ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) && ((uintptr_t)B % 16 == 0) && (ldb % 4 == 0);
+  gram32_kernel<<<grid, 256, kG32Smem, st>>>(A, m, (int)n, lda, nullptr, groups, partial, B, ldb, vec);
   return cudaGetLastError();
 }
 
