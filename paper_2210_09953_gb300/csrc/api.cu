@@ -75,6 +75,7 @@ size_t stage_workspace(int64_t m, int64_t n, int64_t k, int prec) {
   s = std::max(s, small_qr_workspace(k, n));
   s = std::max(s, gram_workspace(m, n));
   s = std::max(s, trsm_workspace(m, n, prec));
+  if (prec != RCQR_F64 && trsm32_gram_supported(n)) s = std::max(s, trsm32_gram_workspace(m, n));
   s = std::max(s, (size_t)n * n * 8 + 256);
   return s;
 }
@@ -263,10 +264,17 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   }
   // Alg. 2 step 3 / Alg. 7 step 4: for RR the leading block of the
   // de-normalised R is R11 D_sel, so Q = X Pi_{:,1:r} (R11 D_sel)^{-1}.
-  RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream, dev_status));
+  const bool fused = pass2 && prec != RCQR_F64 && trsm32_gram_supported(n);
+  if (fused) {
+    // the substitution and the Gram of Alg. 3 step 2 in one pass over X
+    RCQR_TRY(launch_trsm32_gram(X, m, n, ldx, prec, R, ldr, pm, rkp, (float *)Q, ldq, b.A, n, *scratch(),
+                                stream));
+  } else {
+    RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream, dev_status));
+  }
   if (pass2) {
     // Alg. 3 steps 2-4 on the computed Q
-    RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
+    if (!fused) RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
     RCQR_TRY(launch_chol_update(b.A, n, n, rkp, b.Rp, n, R, ldr, dev_status, stream));
     RCQR_TRY(launch_trsm(Q, m, n, ldq, qprec, b.Rp, n, nullptr, rkp, Q, ldq, *scratch(), stream,
                          dev_status));

@@ -117,6 +117,16 @@ cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int 
 int gram32_groups(int64_t m, int64_t n);
 cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
                           double *partial, int groups, cudaStream_t st);
+// Substitution fused with the second pass's Gram (mixed path, n <= 64): writes Q
+// and A = Q^T Q (FP64, lda).
+bool trsm32_gram_supported(int64_t n);
+size_t trsm32_gram_workspace(int64_t m, int64_t n);
+cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
+                               int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                               double *A, int64_t lda, Workspace &ws, cudaStream_t st);
+// A = sum of `groups` n x n partials (fixed order), trsm_simt.cu.
+cudaError_t launch_gram_reduce(const double *partial, int groups, int64_t n, double *A, int64_t lda,
+                               cudaStream_t st);
 // Reverse mode of the thin QR map (adjoint.cu).
 size_t adjoint_workspace(int64_t m, int64_t n);
 cudaError_t launch_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *R,

@@ -103,6 +103,135 @@ trsm32_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const flo
         if (live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * ldq] = q[t][j];
 }
 
+// ---- Substitution fused with the Gram of the second pass (Alg. 2 step 3 and
+// Alg. 3 step 2, mixed path, NB <= 64).  A persistent CTA takes tiles of 256
+// rows: two rows per thread are substituted as in trsm32_kernel, written to Q
+// and to a shared tile, and the CTA's partial Q^T Q (thread (ti, tj): entries
+// (ti + 16a, tj + 8b)) is accumulated from the tile in 32-row FP32 chunks with
+// compensated chunk sums -- the arithmetic of gram32_kernel -- so Q is not read
+// back from memory.
+constexpr int kTGRows = 2 * kT32Threads;      // rows per tile
+constexpr int kTGStride = kTGRows + 4;        // tile column stride (16-byte aligned rows)
+
+template <class TX, int NB>
+__global__ void __launch_bounds__(kT32Threads)
+trsm32_gram_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const float *__restrict__ Rf,
+                   const float *__restrict__ dinv, const int32_t *__restrict__ perm,
+                   const int64_t *__restrict__ rank, float *Q, int64_t ldq, double *__restrict__ partial) {
+  static_assert(NB <= 64, "one 64 x 64 Gram tile");
+  extern __shared__ float4 tg_smem4[];
+  float *Rs = reinterpret_cast<float *>(tg_smem4);
+  float *Ds = Rs + NB * NB;
+  float *Ts = Ds + 64;                         // 64 columns x kTGStride (columns >= NB stay zero)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB / 4; e += blockDim.x) tg_smem4[e] = reinterpret_cast<const float4 *>(Rf)[e];
+  for (int j = tid; j < 64; j += blockDim.x) Ds[j] = j < NB ? dinv[j] : 0.0f;
+  for (int e = tid; e < 64 * kTGStride; e += blockDim.x) Ts[e] = 0.0f;
+  __syncthreads();
+  const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
+  const int ti = tid & 15, tj = tid >> 4;
+  float outer[4][8], comp[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) outer[a][b] = comp[a][b] = 0.0f;
+  const int64_t tiles = (m + kTGRows - 1) / kTGRows;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTGRows + tid;
+    {
+      bool live[2];
+      live[0] = row0 < m;
+      live[1] = row0 + kT32Threads < m;
+      float q[2][NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int src = (perm && j < r) ? perm[j] : j;
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+          q[t][j] = (j < r && live[t]) ? to_f32(X[row0 + (int64_t)t * kT32Threads + (int64_t)src * ldx]) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const float *rc = Rs + j * NB;
+        float s[2] = {q[0][j], q[1][j]};
+#pragma unroll
+        for (int i4 = 0; i4 < j / 4; ++i4) {
+          const float4 rv = *reinterpret_cast<const float4 *>(rc + 4 * i4);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            s[t] = fmaf(-q[t][4 * i4 + 0], rv.x, s[t]);
+            s[t] = fmaf(-q[t][4 * i4 + 1], rv.y, s[t]);
+            s[t] = fmaf(-q[t][4 * i4 + 2], rv.z, s[t]);
+            s[t] = fmaf(-q[t][4 * i4 + 3], rv.w, s[t]);
+          }
+        }
+#pragma unroll
+        for (int i = (j / 4) * 4; i < j; ++i) {
+          const float rvi = rc[i];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) s[t] = fmaf(-q[t][i], rvi, s[t]);
+        }
+        const float dj = Ds[j];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) q[t][j] = s[t] * dj;
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (j < n && live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * ldq] = q[t][j];
+          Ts[j * kTGStride + tid + t * kT32Threads] = q[t][j];
+        }
+      }
+    }
+    __syncthreads();
+    // partial Gram of the tile: eight 32-row chunks, each summed in FP32 and added compensated
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTGRows; c0 += 32) {
+      float inner[4][8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) inner[a][b] = 0.0f;
+#pragma unroll 2
+      for (int s4 = 0; s4 < 8; ++s4) {
+        const int rr = c0 + 4 * s4;
+        float4 va[4], vb[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) va[a] = *reinterpret_cast<const float4 *>(Ts + (ti + 16 * a) * kTGStride + rr);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) vb[b] = *reinterpret_cast<const float4 *>(Ts + (tj + 8 * b) * kTGStride + rr);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            inner[a][b] = fmaf(va[a].x, vb[b].x, inner[a][b]);
+            inner[a][b] = fmaf(va[a].y, vb[b].y, inner[a][b]);
+            inner[a][b] = fmaf(va[a].z, vb[b].z, inner[a][b]);
+            inner[a][b] = fmaf(va[a].w, vb[b].w, inner[a][b]);
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float y = inner[a][b] - comp[a][b];
+          const float tt = outer[a][b] + y;
+          comp[a][b] = (tt - outer[a][b]) - y;
+          outer[a][b] = tt;
+        }
+    }
+    __syncthreads();   // the tile is rewritten by the next iteration
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ti + 16 * a, j = tj + 8 * b;
+      if (i < n && j < n) partial[((int64_t)blockIdx.x * n + j) * n + i] = (double)outer[a][b] - (double)comp[a][b];
+    }
+}
+
 // ---- Gram A = Q^T Q in FP32 with compensated chunk sums
 constexpr int kG32Rows = 64;     // rows per shared-memory chunk
 constexpr int kG32Stride = 68;   // column stride in shared memory (16-byte rows, conflict-free quads)
@@ -307,6 +436,61 @@ cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int 
     return launch_trsm32_t<__nv_bfloat16>((const __nv_bfloat16 *)X, m, n, ldx, Rf, dinv, perm, rank,
                                           (float *)Q, ldq, NB, st);
   return launch_trsm32_t<float>((const float *)X, m, n, ldx, Rf, dinv, perm, rank, (float *)Q, ldq, NB, st);
+}
+
+bool trsm32_gram_supported(int64_t n) { return n >= 1 && n <= 64; }
+
+int trsm32_gram_groups(int64_t m) {
+  const int64_t tiles = (m + kTGRows - 1) / kTGRows;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(2LL * num_sms(), tiles));
+}
+
+size_t trsm32_gram_workspace(int64_t m, int64_t n) {
+  Workspace w(nullptr, 0);
+  w.take<float>((size_t)64 * 64);
+  w.take<float>((size_t)64);
+  w.take<double>((size_t)trsm32_gram_groups(m) * n * n);
+  return w.used;
+}
+
+cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
+                               int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                               double *A, int64_t lda, Workspace &ws, cudaStream_t st) {
+  const int NB = (int)((n + 15) / 16) * 16;
+  float *Rf = ws.take<float>((size_t)64 * 64);
+  float *dinv = ws.take<float>((size_t)64);
+  const int G = trsm32_gram_groups(m);
+  double *partial = ws.take<double>((size_t)G * n * n);
+  if (!Rf || !dinv || !partial) return cudaErrorMemoryAllocation;
+  trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
+  const size_t smem = ((size_t)NB * NB + 64 + (size_t)64 * kTGStride) * sizeof(float);
+  cudaError_t e = cudaSuccess;
+#define RCQR_TG(NBV)                                                                                     \
+  case NBV: {                                                                                            \
+    if (prec == RCQR_BF16) {                                                                             \
+      e = set_smem(trsm32_gram_kernel<__nv_bfloat16, NBV>, (int)smem);                                   \
+      if (e != cudaSuccess) return e;                                                                    \
+      trsm32_gram_kernel<__nv_bfloat16, NBV><<<G, kT32Threads, smem, st>>>(                              \
+          (const __nv_bfloat16 *)X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial);              \
+    } else {                                                                                             \
+      e = set_smem(trsm32_gram_kernel<float, NBV>, (int)smem);                                           \
+      if (e != cudaSuccess) return e;                                                                    \
+      trsm32_gram_kernel<float, NBV><<<G, kT32Threads, smem, st>>>((const float *)X, m, (int)n, ldx, Rf, \
+                                                                   dinv, perm, rank, Q, ldq, partial);   \
+    }                                                                                                    \
+    break;                                                                                               \
+  }
+  switch (NB) {
+    RCQR_TG(16)
+    RCQR_TG(32)
+    RCQR_TG(48)
+    RCQR_TG(64)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RCQR_TG
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_gram_reduce(partial, G, n, A, lda, st);
 }
 
 int gram32_groups(int64_t m, int64_t n) {

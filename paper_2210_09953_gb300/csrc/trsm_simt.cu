@@ -157,6 +157,12 @@ cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   return cudaGetLastError();
 }
 
+cudaError_t launch_gram_reduce(const double *partial, int groups, int64_t n, double *A, int64_t lda,
+                               cudaStream_t st) {
+  gram_reduce_kernel<<<(unsigned)((n * n * 32 + 255) / 256), 256, 0, st>>>(partial, groups, (int)n, A, lda);
+  return cudaGetLastError();
+}
+
 size_t gram_workspace(int64_t m, int64_t n) {
   Workspace w(nullptr, 0);
   w.take<double>((size_t)std::max(gram_groups(m, n), gram32_groups(m, n)) * n * n);
