@@ -2,38 +2,44 @@
 //
 // Theta's entries are the integer levels T[t] in [-127, 127] (scaled by
 // 1/sqrt(k v) afterwards), i.e. 7-bit integers, exact in bf16.  X is cut, per
-// 1024-row block and column, into S signed digit slices relative to the
-// block's largest exponent e: with t = x 2^(6-e) in (-128, 128), slice b holds
-// a multiple of 2^(-7b) of magnitude <= 128 2^(-7b) (an error-free splitting
-// in the manner of Ozaki et al.; round-to-nearest digits for FP32/BF16 X,
-// truncated 7-bit digits of the FP64 significand).  Each slice is a bf16
-// operand with at most 8 significant bits, every product T*d is below 2^14
-// units of its slice, so the fp32 tensor-core sums over 1024 rows stay below
-// 2^24 units and are exact.  The first NE slices get their own TMEM
-// accumulators (exact); the remaining ones share one accumulator whose fp32
-// rounding over a block stays ~2^-39 (FP32 X: 3 exact of 5 slices) / 2^-46
-// (FP64 X: 4 exact of 8) below the block's largest |x|; BF16 X needs 3
-// slices.  After every block the accumulators are read from TMEM, combined
-// into one int64 per entry and added into a per-column block-floating-point
-// int64 accumulator (the "simple addition" of Sec. 3.1 done exactly, up to
-// one truncation of ~2^-52 relative per block).
+// block of rows and column, into S signed digit slices relative to the
+// block's largest exponent e (an error-free splitting in the manner of Ozaki
+// et al.):
+//   * FP32 / BF16 X: t = x 2^(5-e) in (-64, 64); slice b < S-1 is the
+//     remainder rounded to a multiple of 2^(-7b), so every such digit is at most
+//     64 units of its slice and every product T d is below 2^13 units: the fp32
+//     tensor-core sums over a 2048-row block are exact; the last slice is the
+//     remainder rounded to bf16 (it goes to the shared, rounded accumulator);
+//   * FP64 X: the truncated 7-bit digits of |x| 2^(55-e), products below 2^14,
+//     1024-row blocks.
+// Each slice is a bf16 operand with at most 8 significant bits.  The first NE
+// slices get their own TMEM accumulators (exact); the remaining ones share one
+// accumulator whose fp32 rounding over a block stays ~2^-38 (FP32 X: 3 exact
+// of 5 slices) / 2^-46 (FP64 X: 4 exact of 8) below the block's largest |x|;
+// BF16 X needs 3 slices.  After every block the accumulators are read from
+// TMEM, combined into one int64 per entry and added into a per-column
+// block-floating-point int64 accumulator (the "simple addition" of Sec. 3.1
+// done exactly, up to one truncation of ~2^-52 relative per block).
 //
 // Per CTA: a contiguous run of blocks (split-K over m), KCH chunks of 128
-// rows of Theta and NC columns of X.  The CTA is warp-specialised around a
-// ring of D shared-memory stages of 32 rows each:
-//   * 8 Theta warps generate the Theta tile of a stage (Philox4x32-10 and the
-//     level table, replicated per lane) in the K-major core-matrix layout;
-//   * 7 X warps copy the X rows of a stage three stages ahead into a small
-//     ring (cp.async, no registers held), then cut them into slices with the
-//     block's column exponents (found beforehand by block_exp_kernel);
-//   * one MMA warp waits for a stage to be full, issues its MMAs
-//     (M = 128, N = NC, K = 16) from one thread and commits them to the
-//     stage's "empty" barrier (and after a block's last stage, to the
-//     "accumulators full" barrier).
-// At a block boundary every warp folds TMEM into the int64 accumulators (kept
-// in the workspace, L2-resident) once the producers have filled the first D
-// stages of the next block.  Every wait is bounded; a timeout marks the
-// partial sums NaN and raises RCQR_ETIMEOUT in the status word.
+// rows of Theta and NC columns of X.  The CTA's 16 warps are specialised
+// around a ring of D shared-memory stages of 32 rows each:
+//   * 4 KCH Theta warps generate the Theta tile of a stage (Philox4x32-10 with
+//     the round keys as kernel parameters, the level table replicated per lane)
+//     in the K-major core-matrix layout;
+//   * the other producer warps (12 in all) copy the X rows of a stage three
+//     stages ahead into a small ring (cp.async, no registers held), then cut
+//     them into slices with the block's column exponents (found beforehand by
+//     block_exp_kernel);
+//   * warp 15 waits for a stage to be full and issues its MMAs from one thread
+//     (M = 128, K = 16; the exact slices of a group stacked along N, up to 256),
+//     committing them to the stage's "empty" barrier and, after a block's last
+//     stage, to the "accumulators full" barrier;
+//   * warps 12..15 (one per TMEM lane quadrant) fold TMEM into the int64
+//     accumulators (kept in the workspace, L2-resident) once a block's MMAs
+//     are done; the producers never wait for a fold, only for ring slots.
+// Every wait is bounded; a timeout marks the partial sums NaN and raises
+// RCQR_ETIMEOUT in the status word.
 #include <algorithm>
 
 #include "common.cuh"
@@ -47,13 +53,15 @@ __constant__ int8_t c_theta_levels[256];
 
 namespace {
 
-constexpr int kThetaWarps = 8;                      // Theta tile producers
-constexpr int kXWarps = 7;                          // X slice producers
-constexpr int kProdWarps = kThetaWarps + kXWarps;   // all of them arrive on "full"
-constexpr int kThreadsTC = 32 * (kProdWarps + 1);   // + the MMA warp
-constexpr int kBlockRows = 1024;                    // rows per exponent block / TMEM promotion
+constexpr int kThreadsTC = 512;                     // 16 warps
+constexpr int kProdWarps = 12;                      // warps 0..11 produce (Theta, then X); they arrive on "full"
+constexpr int kFoldWarp0 = 12;                      // warps 12..15 fold TMEM (one per lane quadrant);
+                                                    // warp 15 also issues the MMAs
+// Rows per exponent block / TMEM promotion: products T d stay below 2^13
+// (FP32/BF16: |d| <= 64) or 2^14 (FP64: 7-bit digits), so the fp32 sums are
+// exact over 2048 or 1024 rows.
+constexpr int block_rows(int prec) { return prec == RCQR_F64 ? 1024 : 2048; }
 constexpr int kBK = 32;                             // rows of X per stage
-constexpr int kSPB = kBlockRows / kBK;              // stages per block
 constexpr int kMaxStages = 6;
 constexpr int kTableBytes = 256 * 32 * 4;           // level table, one copy per lane
 constexpr uint32_t kWaitPolls = 1u << 22;          // polls with sleeps of up to 256 ns: about 1 s
@@ -94,7 +102,7 @@ struct TcArgs {
   uint32_t stream_id;
   uint32_t rk[20];    // Philox round keys of the seed (see philox4x32_10_keys)
   int64_t row_offset;
-  int64_t blk0;       // first 1024-row block (global index)
+  int64_t blk0;       // first block of rows (global index)
   int64_t nblk;       // blocks covering [row_offset, row_offset + m)
   int groups;         // CTAs along m
   int ngrp;           // column groups
@@ -221,11 +229,12 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
       *reinterpret_cast<uint4 *>(dst + b * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   } else {
-    // FP32 / BF16 storage: t = x 2^(6-e); digit b = t rounded to a multiple of
-    // 2^(-7b) by adding and removing 1.5 2^(23-7b); t -= digit (both exact).
-    // Pairs of rows go through the packed f32x2 unit.
+    // FP32 / BF16 storage: t = x 2^(5-e) in (-64, 64); digit b = t rounded to a
+    // multiple of 2^(-7b) by adding and removing 1.5 2^(23-7b); t -= digit (both
+    // exact), so every digit is at most 64 in units of its slice.  Pairs of rows
+    // go through the packed f32x2 unit.
     float t8[8];
-    const int sh = 6 - e;
+    const int sh = 5 - e;
     const bool empty = e == EMPTY_EXP;
     const float s1 = empty ? 0.0f : pow2f(sh / 2), s2 = empty ? 0.0f : pow2f(sh - sh / 2);
 #pragma unroll
@@ -242,7 +251,7 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
       mul2(t8[2 * p], t8[2 * p + 1], x0, x1, s2, s2);
     }
 #pragma unroll
-    for (int b = 0; b < S; ++b) {
+    for (int b = 0; b < S - 1; ++b) {
       const float M = __uint_as_float(((uint32_t)(150 - 7 * b) << 23) | 0x400000u);   // 1.5 2^(23-7b)
       uint32_t w[4];
 #pragma unroll
@@ -250,47 +259,76 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
         float u0, u1, d0, d1;
         add2(u0, u1, t8[2 * p], t8[2 * p + 1], M, M);
         add2(d0, d1, u0, u1, -M, -M);
-        if (b + 1 < S) add2(t8[2 * p], t8[2 * p + 1], t8[2 * p], t8[2 * p + 1], -d0, -d1);
+        add2(t8[2 * p], t8[2 * p + 1], t8[2 * p], t8[2 * p + 1], -d0, -d1);
         w[p] = __byte_perm(__float_as_uint(d0), __float_as_uint(d1), 0x7632);
       }
       *reinterpret_cast<uint4 *>(dst + b * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // the last slice feeds the shared (rounded) accumulator: the remainder itself,
+    // rounded to bf16 (8 significant bits relative to the remainder)
+    {
+      uint32_t w[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(t8[2 * p], t8[2 * p + 1]);
+        w[p] = *reinterpret_cast<const uint32_t *>(&h);
+      }
+      *reinterpret_cast<uint4 *>(dst + (S - 1) * slice_stride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
 
 // The Theta tile of one stage: KCH * 128 rows of Theta x 32 rows of X, one
-// Philox call per 16 X rows.  tt indexes the Theta threads.
-template <int KCH>
-__device__ __forceinline__ void theta_tile(unsigned char *sA, const uint32_t *tabp, int tt, int64_t r0, int kgi,
-                                           const TcArgs &a) {
-  constexpr int cpr = kBK / 16;
-  constexpr int calls = KCH * 128 * cpr;
-#pragma unroll 2
-  for (int ci = tt; ci < calls; ci += 32 * kThetaWarps) {
-    const int qq = ci % cpr, row = ci / cpr;
-    const int c = row >> 7, il = row & 127;
-    const int i = (kgi * KCH + c) * 128 + il;
-    uint32_t wv[8];
-    if (i < a.k) {
-      const uint64_t q = (uint64_t)(r0 / 16 + qq);
-      const uint4 w = philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)i, a.stream_id), a.rk);
-      const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+// Philox call per 16 X rows, spread over the NTW Theta warps (CPT calls per
+// thread); each call's Theta row, 16-row sub-block and place in the tile are
+// the same at every stage, so they are computed once.
+template <int KCH, int NTW>
+struct ThetaCalls {
+  static constexpr int CPR = kBK / 16;                       // calls per Theta row and stage
+  static constexpr int CPT = KCH * 128 * CPR / (32 * NTW);
+  static_assert(CPT * 32 * NTW == KCH * 128 * CPR, "calls divide evenly");
+  uint32_t row[CPT];   // Theta row i of the call (>= k: a zero row)
+  uint32_t qq[CPT];    // 16-row sub-block within the stage
+  uint32_t off[CPT];   // byte offset of the call's first 16 bytes in the tile
+
+  __device__ __forceinline__ void init(int tt, int kgi) {
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const uint32_t word = ww[p >> 1];
-        const uint32_t b0 = __byte_perm(word, 0u, 0x4440u + 2u * (p & 1));
-        const uint32_t b1 = __byte_perm(word, 0u, 0x4441u + 2u * (p & 1));
-        wv[p] = __byte_perm(tabp[b0 << 5], tabp[b1 << 5], 0x5410);
-      }
-    } else {
-#pragma unroll
-      for (int p = 0; p < 8; ++p) wv[p] = 0u;
+    for (int u = 0; u < CPT; ++u) {
+      const int ci = tt + 32 * NTW * u;
+      const int q = ci % CPR, r = ci / CPR;
+      const int c = r >> 7, il = r & 127;
+      row[u] = (uint32_t)((kgi * KCH + c) * 128 + il);
+      qq[u] = (uint32_t)q;
+      off[u] = (uint32_t)(c * (128 * kBK * 2) + (il >> 3) * (kBK * 16) + (il & 7) * 16 + 2 * q * 128);
     }
-    unsigned char *dst = sA + c * (128 * kBK * 2) + (il >> 3) * (kBK * 16) + (il & 7) * 16;
-    *reinterpret_cast<uint4 *>(dst + (2 * qq) * 128) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-    *reinterpret_cast<uint4 *>(dst + (2 * qq + 1) * 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
   }
-}
+
+  __device__ __forceinline__ void tile(unsigned char *sA, const uint32_t *tabp, int64_t r0, const TcArgs &a) const {
+    const uint64_t qbase = (uint64_t)(r0 / 16);
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      uint32_t wv[8];
+      if (row[u] < (uint32_t)a.k) {
+        const uint64_t q = qbase + qq[u];
+        const uint4 w = philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), row[u], a.stream_id), a.rk);
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const uint32_t word = ww[p >> 1];
+          const uint32_t b0 = __byte_perm(word, 0u, 0x4440u + 2u * (p & 1));
+          const uint32_t b1 = __byte_perm(word, 0u, 0x4441u + 2u * (p & 1));
+          wv[p] = __byte_perm(tabp[b0 << 5], tabp[b1 << 5], 0x5410);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) wv[p] = 0u;
+      }
+      unsigned char *dst = sA + off[u];
+      *reinterpret_cast<uint4 *>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      *reinterpret_cast<uint4 *>(dst + 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+  }
+};
 
 // Bounded mbarrier wait with growing sleeps between polls (a waiting warp
 // leaves the issue slots to the working ones); gives up at once when another
@@ -307,12 +345,6 @@ __device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int
   *f = 1;
 }
 
-// Stage after which the producers fold block b: D stages into block b + 1
-// (the ring is then full and waits for the MMAs of block b + 1), or the end.
-__device__ __forceinline__ int epilogue_trigger(int b, int NB, int D) {
-  return b + 1 < NB ? (b + 1) * kSPB + D - 1 : NB * kSPB - 1;
-}
-
 template <int PREC, int KCH, int JCH>
 struct Tc {
   using Cfg = SliceCfg<PREC>;
@@ -320,8 +352,12 @@ struct Tc {
   using MaxT = typename Cfg::MaxT;
   static constexpr int S = Cfg::S, NE = Cfg::NE, LS = Cfg::LS;
   static constexpr int NACC = NE + 1;
+  static constexpr int BR = block_rows(PREC);          // rows per block
+  static constexpr int SPB = BR / kBK;                 // stages per block
+  static constexpr int TOP = PREC == RCQR_F64 ? 6 : 5; // x = t 2^(e - TOP), t the scaled value sliced
   static constexpr int NC = 64 * JCH;                 // columns per CTA
-  static constexpr int CW = NC / 4;                   // columns per thread in the fold
+  static constexpr int NTW = 4 * KCH;                 // Theta warps (two Philox calls per thread and stage)
+  static constexpr int NXW = kProdWarps - NTW;        // X warps
   static constexpr uint32_t NCOLS = (KCH * NACC * NC) <= 256 ? 256u : 512u;
   static constexpr int A_BYTES = KCH * 128 * kBK * 2;
   static constexpr int B_BYTES = S * NC * kBK * 2;
@@ -334,97 +370,110 @@ struct Tc {
     uint64_t accf;
     uint32_t tslot;
     int s_fail;
-    int e_col[2][NC];    // column exponents of the blocks in flight (by block parity)
     int E_col[2][NC];    // running exponents of the int64 accumulators (by block parity)
+    int e_blk[NC];       // the folded block's column exponents
   };
 
-  // Folds block b's TMEM accumulators into the int64 accumulators (all threads).
-  static __device__ __noinline__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc, const TcArgs &a, int kgi,
-                              int col0, int g) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Folds block b's TMEM accumulators into the int64 accumulators.  Run by the
+  // four fold warps (warp w reads TMEM lanes 32 (w % 4) ..); each thread owns one
+  // Theta row of every chunk and all NC columns.  Ends with a barrier of the
+  // fold warps, after which TMEM may be overwritten.
+  static __device__ __noinline__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc,
+                                           const TcArgs &a, int kgi, int col0, int g, int64_t blk) {
+    const int ft = threadIdx.x - 32 * kFoldWarp0, lane = threadIdx.x & 31, lq = (threadIdx.x >> 5) & 3;
+    const int *eb = a.eblk + (blk - a.blk0) * a.n;
+    for (int jl = ft; jl < NC; jl += 128) sh.e_blk[jl] = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
     wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256);
     umma::fence_after_sync();
+    umma::named_sync(128);
     const bool last = b == NB - 1;
     const int p = b & 1;
-    if (warp < 16) {
-      const int lq = warp & 3, cq = warp >> 2;
-      const int il = 32 * lq + lane;
+    const int il = 32 * lq + lane;
+    // chunks of 8 columns; this thread's 8 accumulators of a chunk are contiguous,
+    // Acc[(c 128 + il) NC + jl], and the next chunk's are loaded while this one is folded
+    constexpr int CPC = NC / 8, NCH = KCH * CPC;
+    auto acc_ptr = [&](int ch) {
+      return reinterpret_cast<longlong2 *>(Acc + ((size_t)(ch / CPC) * 128 + il) * NC + (ch % CPC) * 8);
+    };
+    longlong2 nxt[4];
+    if (b > 0) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(0)[h];
+    }
 #pragma unroll 1
-      for (int jc0 = 0; jc0 < CW; jc0 += 8) {
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int c = ch / CPC, jc0 = (ch % CPC) * 8;
+      const int i = (kgi * KCH + c) * 128 + il;
+      longlong2 old2[4];
 #pragma unroll
-        for (int c = 0; c < KCH; ++c) {
-          // this thread's 8 accumulators of the chunk are contiguous: Acc[(c 128 + il) NC + jl]
-          longlong2 *ap = reinterpret_cast<longlong2 *>(Acc + ((size_t)c * 128 + il) * NC + cq * CW + jc0);
-          longlong2 old2[4];
-          if (b > 0) {
+      for (int h = 0; h < 4; ++h) old2[h] = nxt[h];
+      if (b > 0 && ch + 1 < NCH) {
 #pragma unroll
-            for (int h = 0; h < 4; ++h) old2[h] = ap[h];
-          }
-          uint32_t rv[NACC][8];
+        for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(ch + 1)[h];
+      }
+      uint32_t rv[NACC][8];
 #pragma unroll
-          for (int acc = 0; acc < NACC; ++acc)
-            umma::tmem_ld8(tbase + ((uint32_t)(32 * lq) << 16) + (uint32_t)((c * NACC + acc) * NC + cq * CW + jc0),
-                           rv[acc]);
-          umma::tmem_wait_ld();
-          const int i = (kgi * KCH + c) * 128 + il;
-          long long out[8];
+      for (int acc = 0; acc < NACC; ++acc)
+        umma::tmem_ld8(tbase + ((uint32_t)(32 * lq) << 16) + (uint32_t)((c * NACC + acc) * NC + jc0), rv[acc]);
+      umma::tmem_wait_ld();
+      long long out[8];
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int jl = cq * CW + jc0 + jj;
-            const int e = sh.e_col[p][jl];
-            const int Ec = sh.E_col[p][jl];
-            const long long old = b > 0 ? ((jj & 1) ? old2[jj >> 1].y : old2[jj >> 1].x) : 0LL;
-            long long acc_v;
-            int En;
-            if (e == EMPTY_EXP) {
-              En = Ec;
-              acc_v = Ec == EMPTY_EXP ? 0LL : old;
-            } else {
-              long long V = 0;
+      for (int jj = 0; jj < 8; ++jj) {
+        const int jl = jc0 + jj;
+        const int e = sh.e_blk[jl];
+        const int Ec = sh.E_col[p][jl];
+        const long long old = b > 0 ? ((jj & 1) ? old2[jj >> 1].y : old2[jj >> 1].x) : 0LL;
+        long long acc_v;
+        int En;
+        if (e == EMPTY_EXP) {
+          En = Ec;
+          acc_v = Ec == EMPTY_EXP ? 0LL : old;
+        } else {
+          long long V = 0;
 #pragma unroll
-              for (int bs = 0; bs < NE; ++bs)
-                V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
-              V += __float2ll_rn(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));
-              const int f = e - 6 - 7 * NE - LS;
-              if (Ec == EMPTY_EXP) {
-                acc_v = V;
-                En = f;
-              } else if (f >= Ec) {
-                const int s = f - Ec;
-                acc_v = (s >= 63 ? (old < 0 ? -1LL : 0LL) : (old >> s)) + V;
-                En = f;
-              } else {
-                const int s = Ec - f;
-                acc_v = old + (s >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> s));
-                En = Ec;
-              }
-            }
-            out[jj] = acc_v;
-            if (last) {
-              const int j = col0 + jl;
-              if (i < a.k && j < a.n)
-                a.partial[((int64_t)g * a.n + j) * a.k + i] = En == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, En);
-            }
-          }
-          if (!last) {
-#pragma unroll
-            for (int h = 0; h < 4; ++h) ap[h] = make_longlong2(out[2 * h], out[2 * h + 1]);
+          for (int bs = 0; bs < NE; ++bs)
+            V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
+          V += __float2ll_rn(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));
+          const int f = e - TOP - 7 * NE - LS;
+          if (Ec == EMPTY_EXP) {
+            acc_v = V;
+            En = f;
+          } else if (f >= Ec) {
+            const int sft = f - Ec;
+            acc_v = (sft >= 63 ? (old < 0 ? -1LL : 0LL) : (old >> sft)) + V;
+            En = f;
+          } else {
+            const int sft = Ec - f;
+            acc_v = old + (sft >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> sft));
+            En = Ec;
           }
         }
+        out[jj] = acc_v;
+        if (last) {
+          const int j = col0 + jl;
+          if (i < a.k && j < a.n)
+            a.partial[((int64_t)g * a.n + j) * a.k + i] = En == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, En);
+        }
+      }
+      if (!last) {
+        longlong2 *ap = acc_ptr(ch);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) ap[h] = make_longlong2(out[2 * h], out[2 * h + 1]);
       }
     }
     // running exponents after this block
-    for (int jl = tid; jl < NC; jl += kThreadsTC) {
-      const int e = sh.e_col[p][jl], Ec = sh.E_col[p][jl];
+    for (int jl = ft; jl < NC; jl += 128) {
+      const int e = sh.e_blk[jl];
+      const int Ec = sh.E_col[p][jl];
       int En = Ec;
       if (e != EMPTY_EXP) {
-        const int f = e - 6 - 7 * NE - LS;
+        const int f = e - TOP - 7 * NE - LS;
         En = (Ec == EMPTY_EXP || f > Ec) ? f : Ec;
       }
       sh.E_col[p ^ 1][jl] = En;
     }
     umma::fence_before_sync();
-    umma::named_sync(kThreadsTC);
+    umma::named_sync(128);
   }
 };
 
@@ -438,21 +487,21 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Column exponents of every 1024-row block: eblk[(blk - blk0) * n + j].  One
+// Column exponents of every block of br rows: eblk[(blk - blk0) * n + j].  One
 // warp per (block, column), 8 per CTA; the rows outside [0, m) are skipped.
 template <class T>
 __global__ void __launch_bounds__(256) block_exp_kernel(const T *__restrict__ X, int64_t m, int n, int64_t ldx,
-                                                        int64_t row_offset, int64_t blk0, int64_t nblk,
+                                                        int64_t row_offset, int64_t blk0, int64_t nblk, int br,
                                                         int *__restrict__ eblk) {
   const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= nblk * n) return;
   const int64_t bl = w / n;
   const int j = (int)(w % n);
-  const int64_t lr0 = (blk0 + bl) * kBlockRows - row_offset;
+  const int64_t lr0 = (blk0 + bl) * br - row_offset;
   const T *col = X + (int64_t)j * ldx;
   decltype(mag_bits(T(0))) mx = 0;
-  for (int r = lane; r < kBlockRows; r += 32) {
+  for (int r = lane; r < br; r += 32) {
     const int64_t lr = lr0 + r;
     if (lr >= 0 && lr < m) mx = max(mx, mag_bits(__ldg(col + lr)));
   }
@@ -466,9 +515,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   using K = Tc<PREC, KCH, JCH>;
   using T = typename K::T;
   constexpr int NC = K::NC, S = K::S;
+  constexpr int NTW = K::NTW, NXW = K::NXW;
   constexpr int NTASK = 4 * NC;                        // (column, 8-row octet) pairs per stage
-  constexpr int NXT = 32 * kXWarps;
-  constexpr int TPT = (NTASK + NXT - 1) / NXT;         // tasks per X thread (the last ones partial)
+  constexpr int NXT = 32 * NXW;
+  constexpr int TPT = NTASK / NXT;                     // tasks per X thread
+  static_assert(TPT * NXT == NTASK, "X tasks divide evenly");
   constexpr int H = (int)(8 * sizeof(T) / 16);         // 16-byte chunks per octet
   constexpr int SLOT_BYTES = NTASK * 8 * (int)sizeof(T);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -487,6 +538,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   const int64_t bb = a.blk0 + (a.nblk * g) / a.groups;
   const int64_t be_ = a.blk0 + (a.nblk * (g + 1)) / a.groups;
   const int NB = (int)(be_ - bb);
+  constexpr int kSPB = K::SPB, kBlockRows = K::BR;
   const int total = NB * kSPB;
   long long *Acc = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (KCH * NC * 128);
 
@@ -494,10 +546,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     const int lev = (int)c_theta_levels[e >> 5];
     table[e] = __float_as_uint((float)lev) >> 16;
   }
-  for (int j = tid; j < NC; j += kThreadsTC) {
-    sh.E_col[0][j] = EMPTY_EXP;
-    sh.e_col[0][j] = col0 + j < a.n ? a.eblk[(bb - a.blk0) * a.n + col0 + j] : EMPTY_EXP;
-  }
+  for (int j = tid; j < NC; j += kThreadsTC) sh.E_col[0][j] = EMPTY_EXP;
   if (tid == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       umma::mbar_init(&sh.full[s], kProdWarps);
@@ -512,24 +561,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   umma::fence_after_sync();
   const uint32_t tbase = sh.tslot;
 
-  if (warp < kThetaWarps) {
+  if (warp < NTW) {
     // ---- Theta producers
     const uint32_t *tabp = table + lane;
-    int next = 0;
+    ThetaCalls<KCH, NTW> calls;
+    calls.init(tid, kgi);
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
       const int b = it / kSPB, st = it % kSPB;
-      theta_tile<KCH>(stage_base + slot * K::STAGE_BYTES, tabp, tid, (bb + b) * kBlockRows + st * kBK, kgi, a);
+      calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, (bb + b) * kBlockRows + st * kBK, a);
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
-      if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
     }
   } else if (warp < kProdWarps) {
     // ---- X producers: task o = xt + NXT u is column jl = 8 (o / 32) + o % 8, octet oc = (o / 8) % 4
     // (8 consecutive lanes: 8 consecutive columns of one octet, so the slice stores do not conflict)
-    const int xt = tid - 32 * kThetaWarps;
+    const int xt = tid - 32 * NTW;
     // copies the octet of task o for stage s into ring slot `slot` (asynchronously where possible)
     auto issue = [&](int s, int slot, int o) {
       const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
@@ -551,8 +600,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     for (int s = 0; s < kXAhead; ++s) {
       if (s < total)
 #pragma unroll
-        for (int u = 0; u < TPT; ++u)
-          if (xt + NXT * u < NTASK) issue(s, s % kXSlots, xt + NXT * u);
+        for (int u = 0; u < TPT; ++u) issue(s, s % kXSlots, xt + NXT * u);
       cp_async_commit();
     }
     int e_cur[TPT], e_nxt[TPT];
@@ -560,17 +608,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     for (int u = 0; u < TPT; ++u) {
       const int o = xt + NXT * u;
       const int jl = 8 * (o >> 5) + (o & 7);
-      e_cur[u] = (o < NTASK && col0 + jl < a.n) ? a.eblk[(bb - a.blk0) * a.n + col0 + jl] : EMPTY_EXP;
+      e_cur[u] = col0 + jl < a.n ? a.eblk[(bb - a.blk0) * a.n + col0 + jl] : EMPTY_EXP;
       e_nxt[u] = e_cur[u];
     }
-    int next = 0;
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       const int b = it / kSPB, st = it % kSPB;
       if (it + kXAhead < total)
 #pragma unroll
-        for (int u = 0; u < TPT; ++u)
-          if (xt + NXT * u < NTASK) issue(it + kXAhead, (it + kXAhead) % kXSlots, xt + NXT * u);
+        for (int u = 0; u < TPT; ++u) issue(it + kXAhead, (it + kXAhead) % kXSlots, xt + NXT * u);
       cp_async_commit();
       if (st == kSPB / 2 && b + 1 < NB) {
         // exponents of the next block, read early
@@ -578,16 +624,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
         for (int u = 0; u < TPT; ++u) {
           const int o = xt + NXT * u;
           const int jl = 8 * (o >> 5) + (o & 7);
-          e_nxt[u] = (o < NTASK && col0 + jl < a.n) ? a.eblk[(bb - a.blk0 + b + 1) * a.n + col0 + jl] : EMPTY_EXP;
+          e_nxt[u] = col0 + jl < a.n ? a.eblk[(bb - a.blk0 + b + 1) * a.n + col0 + jl] : EMPTY_EXP;
         }
       }
       if (st == 0 && b > 0) {
 #pragma unroll
-        for (int u = 0; u < TPT; ++u) {
-          const int o = xt + NXT * u;
-          e_cur[u] = e_nxt[u];
-          if (o < NTASK && ((o >> 3) & 3) == 0) sh.e_col[b & 1][8 * (o >> 5) + (o & 7)] = e_cur[u];
-        }
+        for (int u = 0; u < TPT; ++u) e_cur[u] = e_nxt[u];
       }
       cp_async_wait<kXAhead>();
       if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
@@ -596,23 +638,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
 #pragma unroll
       for (int u = 0; u < TPT; ++u) {
         const int o = xt + NXT * u;
-        if (o < NTASK) {
-          const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
-          __align__(16) T v[8];
+        const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
+        __align__(16) T v[8];
 #pragma unroll
-          for (int h = 0; h < H; ++h)
-            reinterpret_cast<uint4 *>(v)[h] = *reinterpret_cast<const uint4 *>(src + h * (NTASK * 16) + o * 16);
-          slice8_store<PREC>(v, e_cur[u], sB + (jl >> 3) * (kBK * 16) + oc * 128 + (jl & 7) * 16, NC * kBK * 2);
-        }
+        for (int h = 0; h < H; ++h)
+          reinterpret_cast<uint4 *>(v)[h] = *reinterpret_cast<const uint4 *>(src + h * (NTASK * 16) + o * 16);
+        slice8_store<PREC>(v, e_cur[u], sB + (jl >> 3) * (kBK * 16) + oc * 128 + (jl & 7) * 16, NC * kBK * 2);
       }
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
-      if (next < NB && it == epilogue_trigger(next, NB, D)) K::fold(sh, next++, NB, tbase, Acc, a, kgi, col0, g);
     }
     cp_async_wait<0>();
+  } else if (warp < kThreadsTC / 32 - 1) {
+    // ---- fold warps 12..14
+    for (int b = 0; b < NB; ++b) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g, bb + b);
   } else {
-    // ---- MMA warp: one thread issues, the warp folds with the others
+    // ---- warp 15: one thread issues the MMAs; after a block's last stage the warp folds with warps 12..14.
     // Slices 0..NE feed consecutive accumulators and sit consecutively in the
     // stage, so up to 256 / NC of them form one MMA with N = (count) NC (the
     // Theta tile is then read once for all of them); the slices below NE add
@@ -650,11 +692,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
         if (st == kSPB - 1) umma::mma_commit(&sh.accf);
       }
       __syncwarp();
-      if (st == kSPB - 1) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g);
+      if (st == kSPB - 1) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g, bb + b);
     }
   }
 
-  // every thread has passed the last fold's barrier: all MMAs and TMEM reads are done
+  // every thread is done: the last fold consumed the last MMAs and read TMEM
+  __syncthreads();
   if (*(volatile int *)&sh.s_fail != 0) {
     for (int e = tid; e < KCH * 128 * NC; e += kThreadsTC) {
       const int il = e % (KCH * 128), jl = e / (KCH * 128);
@@ -682,7 +725,7 @@ __global__ void sketch_tc_reduce_kernel(const double *__restrict__ partial, int 
 }
 
 struct TcPlan {
-  int JCH, NC, ngrp, KCH, kgrp, D, groups, S;
+  int JCH, NC, ngrp, KCH, kgrp, D, groups, S, BR;
   int64_t blk0, nblk;
   size_t smem;
 };
@@ -708,8 +751,9 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   const size_t budget = 220 * 1024 - kTableBytes - ring;
   p.D = (int)std::min<size_t>(kMaxStages, budget / stage);
   p.smem = kTableBytes + ring + (size_t)p.D * stage;
-  p.blk0 = row_offset / kBlockRows;
-  p.nblk = (row_offset + m + kBlockRows - 1) / kBlockRows - p.blk0;
+  p.BR = block_rows(prec);
+  p.blk0 = row_offset / p.BR;
+  p.nblk = (row_offset + m + p.BR - 1) / p.BR - p.blk0;
   const int64_t ctas_per_rows = (int64_t)p.kgrp * p.ngrp;
   int64_t groups = std::max<int64_t>(1, num_sms() / ctas_per_rows);
   groups = std::min<int64_t>(groups, p.nblk);
@@ -804,14 +848,16 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
     const unsigned eg = (unsigned)((p.nblk * n + 7) / 8);
     switch (prec) {
       case RCQR_F64:
-        block_exp_kernel<double><<<eg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk, eblk);
+        block_exp_kernel<double><<<eg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk,
+                                                      p.BR, eblk);
         break;
       case RCQR_F32:
-        block_exp_kernel<float><<<eg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk, eblk);
+        block_exp_kernel<float><<<eg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk,
+                                                     p.BR, eblk);
         break;
       default:
         block_exp_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n, ldx, row_offset,
-                                                            p.blk0, p.nblk, eblk);
+                                                            p.blk0, p.nblk, p.BR, eblk);
     }
   }
   switch (prec) {
