@@ -28,6 +28,13 @@ sys.path.insert(0, ROOT)
 M, N, K, COND = 4194304, 64, 256, 1e8
 SEED_X, SEED_THETA = 1002, 0x5EED0002
 ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (about 10-20 s on 16 cores)
+# DRAM bytes (read + write) of the three kernels of one rcqr_sketch call on the 4M x 64 FP32
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1M-row launch of each kernel,
+# scaled by 4 (per-row traffic is the same), profiles/sketch_call_dram_1Mx64.md.
+SKETCH_CALL_TRAFFIC = 4 * (268452608 + 3247872 + 288038912 + 25882112 + 19934720)
+# the same for trsm32_gram_kernel (X read once, Q written once; the writes still in L2 when
+# the kernel ends are not counted), profiles/sketch_call_dram_1Mx64.md
+TRSM_GRAM_TRAFFIC = 4 * (268790272 + 222318336)
 
 
 def parse():
@@ -222,6 +229,9 @@ def run_ours(args):
     ms_sketch = timed(lambda: rc.rcqr_sketch(X32, K, SEED_THETA, P=P, workspace=ws32), max(3, args.steps), 2)
     R1 = rc.rcqr_small_qr(P, want_S=False)
     ms_trsm = timed(lambda: rc.rcqr_trsm(X32, R1, Q=Q32), max(3, args.steps), 2)
+    # the dominant kernel of the step: the first substitution fused with the Gram (one launch
+    # plus its R preparation and the Gram reduction)
+    ms_tg = timed(lambda: rc.rcqr_trsm_gram(X32, R1, Q=Q32, workspace=ws32), max(3, args.steps), 2)
 
     fp64 = None
     if not args.no_fp64:
@@ -239,19 +249,69 @@ def run_ours(args):
                 "status": int(st64[0])}
         del Q64, ws64
 
-    # end to end through the public call: pinned host X -> device, factor, Q and R back to host
-    Xh = torch.empty((N, m), dtype=torch.float32, pin_memory=True).t()
-    Xh.copy_(X32)
-    Qh = torch.empty((N, m), dtype=torch.float32, pin_memory=True).t()
+    # End to end through the public call, streaming: every step copies its X from pinned host
+    # memory, factors it and copies Q and R back.  Two device buffer sets and three streams let
+    # step s+1's upload and step s-1's download run while step s is factored (the copies of
+    # every timed step are inside the timed region).  Host buffers are flat pinned arrays viewed
+    # column-major, so each transfer is one contiguous copy.
+    Xh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
+    Xh_flat.view(N, m).t().copy_(X32)
+    Qh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
     Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
-    Xd = rc.colmajor(m, N, torch.float32, dev)
+    bufs = []
+    for _ in range(2):
+        Xd = rc.colmajor(m, N, torch.float32, dev)
+        Qd = rc.colmajor(m, N, torch.float32, dev)
+        wsd = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.DIRECT2, rc.F32) + 256, dtype=torch.uint8,
+                          device=dev)
+        bufs.append((Xd, Xd.t().reshape(-1), Qd, Qd.t().reshape(-1), wsd))
+    s_in, s_run, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def step_e2e():
-        Xd.copy_(Xh, non_blocking=True)
-        Qd_, Rd_, _, _, _ = rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32)
-        Qh.copy_(Qd_, non_blocking=True)
-        Rh.copy_(Rd_, non_blocking=True)
-    ms_e2e = timed(step_e2e, max(3, min(args.steps, 5)), 1)
+    def e2e_steps(count):
+        done_out = [None, None]        # event: buffer set's previous Q download finished
+        for s in range(count):
+            Xd, Xf, Qd, Qf, wsd = bufs[s % 2]
+            with torch.cuda.stream(s_in):
+                if done_out[s % 2] is not None:
+                    s_in.wait_event(done_out[s % 2])
+                Xf.copy_(Xh_flat, non_blocking=True)
+                up = torch.cuda.Event()
+                up.record(s_in)
+            with torch.cuda.stream(s_run):
+                s_run.wait_event(up)
+                _, Rd_, _, _, _ = rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Qd, workspace=wsd)
+                ran = torch.cuda.Event()
+                ran.record(s_run)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ran)
+                Qh_flat.copy_(Qf, non_blocking=True)
+                Rh.copy_(Rd_, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_out)
+                done_out[s % 2] = ev
+        for st_ in (s_in, s_run, s_out):
+            stream.wait_stream(st_)
+
+    e2e_steps(2)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for st_ in (s_in, s_run, s_out):
+        st_.wait_stream(stream)
+    e2e_steps(n_e2e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / n_e2e
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t[0])
+    Xf0, Qf0 = bufs[0][1], bufs[0][3]
+    ms_h2d = timed(lambda: Xf0.copy_(Xh_flat, non_blocking=True), 3, 1)
+    ms_d2h = timed(lambda: Qh_flat.copy_(Qf0, non_blocking=True), 3, 1)
 
     peaks = {}
     try:
@@ -262,10 +322,17 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sketch_bytes = m * N * 4                 # algorithmic: X read once
     achieved = sketch_bytes / (ms_sketch * 1e-3) / 1e9
+    # fused substitution + Gram: algorithmic flops per row = 2 (n(n-1)/2 substitution FMAs
+    # + n(n+1)/2 Gram FMAs); FP32 SIMT peak = SMs x 128 FP32 lanes x 2 flops x max SM clock
+    tg_flops = 2.0 * m * (N * (N - 1) // 2 + N * (N + 1) // 2)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = clocks.get("sm_max_mhz") or 2070
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    tg_achieved = tg_flops / (ms_tg * 1e-3) / 1e12
     # per factorization (mixed path, Alg. 3): status reset, sketch (block exponents, tensor-core
-    # sketch, reduction), TSQR leaves + fold, rank, TRSM prep + rows, Gram + reduction,
-    # Cholesky update, TRSM prep + rows
-    launches_per_step = 14
+    # sketch, reduction), Householder R + sign fix, rank, substitution prep + substitution fused
+    # with the Gram + Gram reduction, Cholesky update, substitution prep + substitution
+    launches_per_step = 13
 
     if rank == 0:
         cpu = None
@@ -282,13 +349,21 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"orth_QtQ_minus_I": orth32, "residual_rel_F": res32, "status_ok": ok32},
             "fp64_path": fp64,
-            "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4)},
-            "roofline": {"kernel": "sketch (Theta X, FP32 X)", "bound": "hbm", "achieved": round(achieved, 2),
-                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                         "peak_source": peak_src},
+            "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4), "trsm_gram": round(ms_tg, 4)},
+            "roofline": {"kernel": "trsm32_gram_kernel: Q = X R^-1 fused with A = Q^T Q (rcqr_trsm_gram, FP32 X)",
+                         "bound": "alu", "achieved": round(tg_achieved, 3), "peak": round(alu_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(tg_achieved / alu_peak, 4),
+                         "traffic": TRSM_GRAM_TRAFFIC if m == M else None,
+                         "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "roofline_sketch": {"kernel": "rcqr_sketch: block_exp_kernel + sketch_tc_kernel + reduction (FP32 X)",
+                                "bound": "hbm", "achieved": round(achieved, 2),
+                                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                                "traffic": SKETCH_CALL_TRAFFIC if m == M else None,
+                                "peak_source": peak_src},
             "clocks": clocks,
             "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
-                    "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8},
+                    "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8,
+                    "ms_per_step": round(ms_e2e, 3), "h2d_ms": round(ms_h2d, 3), "d2h_ms": round(ms_d2h, 3)},
             "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
         }

@@ -138,6 +138,18 @@ rcqr_status rcqr_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec
                       const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
                       void *Q, int64_t ldq, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+/* Alg. 2 step 3 and Alg. 3 step 2 in one pass over X (the first substitution of
+ * RCholeskyQR2 with the Gram of its second pass): Q = X R^{-1} as in rcqr_trsm
+ * and A = Q^T Q (n x n double, both triangles), without reading Q back.  Mixed
+ * path only: prec RCQR_F32 or RCQR_BF16 (Q is float), n <= 64; otherwise
+ * RCQR_EUNSUPPORTED.  perm/rank as in rcqr_trsm (A's columns >= rank are 0).
+ * Q may not alias X.  workspace: rcqr_workspace_size(m, n, k, RCQR_DIRECT2, prec)
+ * bytes for any valid k. */
+rcqr_status rcqr_trsm_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                           const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
+                           float *Q, int64_t ldq, double *A, int64_t lda,
+                           void *workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* Gram matrix, Alg. 3 step 2:  A = Q^T Q (n x n double, both triangles), Q of
  * type double (F64) or float (F32, BF16). rank (nullable): only the leading
  * rank x rank block is formed, the rest set to 0. */

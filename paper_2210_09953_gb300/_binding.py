@@ -37,6 +37,8 @@ _SIGS = {
     "rcqr_qrcp": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rcqr_trsm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _sz, _vp]),
     "rcqr_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rcqr_trsm_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _sz,
+                              _vp]),
     "rcqr_chol_update": (_i32, [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
     "rcqr_factor": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _dbl, _vp, _i64, _vp, _i64,
                            _vp, _vp, _vp, _sz, _vp, _vp]),
@@ -159,6 +161,21 @@ def rcqr_trsm(X, R, perm=None, rank=None, Q=None, workspace=None):
     _check("rcqr_trsm", lib.rcqr_trsm(_ptr(X), m, n, _ld(X), prec, _ptr(R), _ld(R), _ptr(perm), _ptr(rank),
                                       _ptr(Q), _ld(Q), wp, wb, _stream()))
     return Q
+
+
+def rcqr_trsm_gram(X, R, perm=None, rank=None, Q=None, workspace=None):
+    """(Q, A): Q = X R^{-1} and A = Q^T Q in one pass (mixed path, n <= 64)."""
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    if Q is None:
+        Q = colmajor(m, n, torch.float32, X.device)
+    A = colmajor(n, n, torch.float64, X.device)
+    ws = workspace if workspace is not None else _workspace(
+        rcqr_workspace_size(m, n, max(8, (n + 7) // 8 * 8), DIRECT2, prec), X.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_trsm_gram", lib.rcqr_trsm_gram(_ptr(X), m, n, _ld(X), prec, _ptr(R), _ld(R), _ptr(perm),
+                                                _ptr(rank), _ptr(Q), _ld(Q), _ptr(A), _ld(A), wp, wb, _stream()))
+    return Q, A
 
 
 def rcqr_gram(Q, rank=None):

@@ -177,6 +177,18 @@ rcqr_status rcqr_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec
   return cuda_status(launch_trsm(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, w, stream));
 }
 
+rcqr_status rcqr_trsm_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
+                           int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                           double *A, int64_t lda, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!X || !R || !Q || !A || !valid_prec(prec) || m < 1 || n < 1 || n > 256 || ldx < m || ldq < m ||
+      ldr < n || lda < n || (const void *)Q == X)
+    return RCQR_EINVAL;
+  if (prec == RCQR_F64 || !trsm32_gram_supported(n)) return RCQR_EUNSUPPORTED;
+  if (!workspace || !aligned(workspace) || ws_bytes < trsm32_gram_workspace(m, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_trsm32_gram(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, A, lda, w, stream));
+}
+
 rcqr_status rcqr_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
                       const int64_t *rank, double *A, int64_t lda, void *workspace,
                       size_t ws_bytes, cudaStream_t stream) {

@@ -322,3 +322,28 @@ def test_reduced_parity(rc, inputs, use_L):
     assert colrel(host64(R), Ro) <= tol
     assert colrel(host64(S), So) <= tol
     assert np.max(np.abs(host64(Z) - Zo)) <= tol * max(1.0, np.max(np.abs(Zo)))
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n", [(70001, 64), (5000, 17), (300, 48)])
+def test_trsm_gram_fused_matches_separate_steps(rc, inputs, prec, m, n):
+    """The fused pass: Q bit-identical to rcqr_trsm (same substitution arithmetic), A within the
+    compensated-Gram bound of the oracle Gram of that Q."""
+    X = inputs.svd_matrix(m, n, 1e6, 900 + n, dtype=prec, device=DEV)
+    k = (4 * n + 7) // 8 * 8
+    R0 = rc.rcqr_small_qr(rc.rcqr_sketch(X, k, 77), want_S=False)
+    Q, A = rc.rcqr_trsm_gram(X, R0)
+    Qs = rc.rcqr_trsm(X, R0)
+    torch.cuda.synchronize()
+    assert torch.equal(Q, Qs)
+    Qh = host64(Q)
+    Ao = Qh.T @ Qh
+    scale = np.abs(Qh).T @ np.abs(Qh)
+    assert np.all(np.abs(host64(A) - Ao) <= 66 * 2.0 ** -24 * scale)
+
+
+def test_trsm_gram_rejects_fp64_and_wide(rc, inputs):
+    X = inputs.svd_matrix(1000, 8, 10.0, 3, dtype="f64", device=DEV)
+    R = inputs.to_colmajor(torch.eye(8, dtype=torch.float64, device=DEV))
+    with pytest.raises(rc.RcqrError):
+        rc.rcqr_trsm_gram(X, R, Q=rc.colmajor(1000, 8, torch.float32, DEV))
