@@ -271,6 +271,16 @@ tsqr_fold_kernel(double *Rleaf, int n, int L, double *R, int64_t ldr, int use_sm
   }
 }
 
+// One level of the fold tree: CTA b folds leaf triangle (2b + 1) stride into
+// leaf 2b stride (in place in the workspace).
+__global__ void __launch_bounds__(kSmallThreads)
+tsqr_pair_kernel(double *Rleaf, int n, int L, int stride) {
+  __shared__ double scal[4];
+  const int64_t t = (int64_t)2 * blockIdx.x * stride, u = t + stride;
+  if (u >= L) return;
+  fold_triangles(Rleaf + t * n * n, Rleaf + u * n * n, n, n, scal);
+}
+
 // Column-pivoted QR of P D^{-1} + rank + de-normalised R.
 __global__ void __launch_bounds__(kSmallThreads)
 qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
@@ -513,11 +523,13 @@ bool fits_smem(int64_t rows, int64_t n) { return copy_bytes(rows, n) <= kSmemLim
 
 // Leaves of the TSQR tree.  Every Householder step is a chain of dependent FP64
 // operations (a reduction, a square root, a division) of a few microseconds on
-// GB300, and a tree of L leaves costs n steps per leaf level plus n per fold,
-// so the sketch is split only when it is much taller than 4n.
+// GB300, and a tree costs n steps per level, so small problems (n <= 64, k <= 4n)
+// are factored by one CTA.  Larger ones are bound by FP64 throughput on that one
+// SM (about k n^2 multiply-adds at ~2 per clock): square leaves spread that work,
+// and the folds run as a binary tree, one level per launch.
 int tsqr_leaves(int64_t k, int64_t n) {
-  if (k <= 4 * n) return 1;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(k / (4 * n), 32));
+  if (n <= 64 && k <= 4 * n) return 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(k / n, 32));
 }
 
 }  // namespace
@@ -541,10 +553,19 @@ cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, d
   const size_t bytes = sm ? copy_bytes(rows_max, n) : 0;
   if (sm) set_smem(tsqr_leaf_kernel, (int)kSmemLimit);
   tsqr_leaf_kernel<<<L, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, L, Rleaf, g, sm);
+  int Lf = L;   // leaves left for the final kernel
   const size_t fold_bytes = (size_t)L * n * (n | 1) * 8;
-  const bool fold_sm = fold_bytes <= kSmemLimit;
+  if (L > 2 && fold_bytes > kSmemLimit) {
+    // binary tree in the workspace; the final kernel sees one triangle
+    for (int stride = 1; stride < L; stride *= 2)
+      tsqr_pair_kernel<<<(unsigned)((L + 2 * stride - 1) / (2 * stride)), kSmallThreads, 0, st>>>(Rleaf, (int)n, L,
+                                                                                                  stride);
+    Lf = 1;
+  }
+  const size_t final_bytes = (size_t)Lf * n * (n | 1) * 8;
+  const bool fold_sm = final_bytes <= kSmemLimit;
   if (fold_sm) set_smem(tsqr_fold_kernel, (int)kSmemLimit);
-  tsqr_fold_kernel<<<1, kSmallThreads, fold_sm ? fold_bytes : 0, st>>>(Rleaf, (int)n, L, R, ldr, fold_sm);
+  tsqr_fold_kernel<<<1, kSmallThreads, fold_sm ? final_bytes : 0, st>>>(Rleaf, (int)n, Lf, R, ldr, fold_sm);
   return cudaGetLastError();
 }
 

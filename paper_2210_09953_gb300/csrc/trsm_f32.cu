@@ -103,6 +103,86 @@ trsm32_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const flo
         if (live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * ldq] = q[t][j];
 }
 
+// ---- Wide R (64 < n <= 256): the row's columns in panels of 64.  A panel is
+// first updated by the earlier panels -- the row's earlier q, re-read from Q
+// (just written by this thread, L2-resident), times a 64 x 64 block of R: 64
+// independent FMA chains per thread -- and then solved against its diagonal
+// block (the triangular part).  Same backward error bound as the row kernel.
+constexpr int kWide = 64;
+
+template <class TX>
+__global__ void __launch_bounds__(kT32Threads)
+trsm32_wide_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const float *__restrict__ Rf, int NB,
+                   const float *__restrict__ dinv, const int32_t *__restrict__ perm,
+                   const int64_t *__restrict__ rank, float *Q, int64_t ldq) {
+  __shared__ __align__(16) float Rb[kWide * kWide];   // off-diagonal block, row-major: Rb[i * 64 + c]
+  __shared__ __align__(16) float Rd[kWide * kWide];   // diagonal block, column-major: Rd[c * 64 + i]
+  __shared__ float Ds[kWide];
+  const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = row < m;
+  const int NP = (n + kWide - 1) / kWide;
+  for (int P = 0; P < NP; ++P) {
+    const int c0 = P * kWide;
+    float acc[kWide];
+#pragma unroll
+    for (int c = 0; c < kWide; ++c) {
+      const int j = c0 + c;
+      acc[c] = 0.0f;
+      if (live && j < r) acc[c] = to_f32(X[row + (int64_t)(perm ? perm[j] : j) * ldx]);
+    }
+    for (int p = 0; p < P; ++p) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kWide * kWide; e += blockDim.x) {
+        const int i = e / kWide, c = e % kWide;
+        Rb[e] = Rf[(p * kWide + i) + (int64_t)(c0 + c) * NB];
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int i = 0; i < kWide; ++i) {
+        const float qi = live ? Q[row + (int64_t)(p * kWide + i) * ldq] : 0.0f;
+        const float4 *rb = reinterpret_cast<const float4 *>(Rb + i * kWide);
+#pragma unroll
+        for (int c4 = 0; c4 < kWide / 4; ++c4) {
+          const float4 rv = rb[c4];
+          acc[4 * c4 + 0] = fmaf(-qi, rv.x, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(-qi, rv.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(-qi, rv.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(-qi, rv.w, acc[4 * c4 + 3]);
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kWide * kWide; e += blockDim.x) {
+      const int c = e / kWide, i = e % kWide;
+      Rd[e] = Rf[(c0 + i) + (int64_t)(c0 + c) * NB];
+    }
+    for (int c = threadIdx.x; c < kWide; c += blockDim.x) Ds[c] = dinv[c0 + c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kWide; ++c) {
+      const float *rc = Rd + c * kWide;
+      float sres = acc[c];
+#pragma unroll
+      for (int i4 = 0; i4 < c / 4; ++i4) {
+        const float4 rv = *reinterpret_cast<const float4 *>(rc + 4 * i4);
+        sres = fmaf(-acc[4 * i4 + 0], rv.x, sres);
+        sres = fmaf(-acc[4 * i4 + 1], rv.y, sres);
+        sres = fmaf(-acc[4 * i4 + 2], rv.z, sres);
+        sres = fmaf(-acc[4 * i4 + 3], rv.w, sres);
+      }
+#pragma unroll
+      for (int i = (c / 4) * 4; i < c; ++i) sres = fmaf(-acc[i], rc[i], sres);
+      acc[c] = sres * Ds[c];
+    }
+    if (live) {
+#pragma unroll
+      for (int c = 0; c < kWide; ++c)
+        if (c0 + c < n) Q[row + (int64_t)(c0 + c) * ldq] = acc[c];
+    }
+  }
+}
+
 // ---- Substitution fused with the Gram of the second pass (Alg. 2 step 3 and
 // Alg. 3 step 2, mixed path, NB <= 64).  A persistent CTA takes tiles of 256
 // rows: two rows per thread are substituted as in trsm32_kernel, written to Q
@@ -402,10 +482,6 @@ cudaError_t launch_trsm32_t(const TX *X, int64_t m, int64_t n, int64_t ldx, cons
     RCQR_T32(32)
     RCQR_T32(48)
     RCQR_T32(64)
-    RCQR_T32(80)
-    RCQR_T32(96)
-    RCQR_T32(112)
-    RCQR_T32(128)
     default: return cudaErrorInvalidValue;
   }
 #undef RCQR_T32
@@ -414,10 +490,14 @@ cudaError_t launch_trsm32_t(const TX *X, int64_t m, int64_t n, int64_t ldx, cons
 
 }  // namespace
 
-bool trsm32_supported(int64_t n) { return n >= 1 && n <= 128; }
+bool trsm32_supported(int64_t n) { return n >= 1 && n <= 256; }
+
+// R in FP32 for the substitution kernels: NB x NB, NB = n rounded up to 16 (row
+// kernel) or to 64 (panel kernel, n > 64).
+int trsm32_nb(int64_t n) { return n > 64 ? (int)((n + 63) / 64) * 64 : (int)((n + 15) / 16) * 16; }
 
 size_t trsm32_workspace(int64_t n) {
-  const int NB = (int)((n + 15) / 16) * 16;
+  const int NB = trsm32_nb(n);
   Workspace w(nullptr, 0);
   w.take<float>((size_t)NB * NB);
   w.take<float>((size_t)NB);
@@ -427,11 +507,21 @@ size_t trsm32_workspace(int64_t n) {
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
                           Workspace &ws, cudaStream_t st) {
-  const int NB = (int)((n + 15) / 16) * 16;
+  const int NB = trsm32_nb(n);
   float *Rf = ws.take<float>((size_t)NB * NB);
   float *dinv = ws.take<float>((size_t)NB);
   if (!Rf || !dinv) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
+  if (n > 64) {
+    const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);
+    if (prec == RCQR_BF16)
+      trsm32_wide_kernel<__nv_bfloat16><<<blocks, kT32Threads, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n, ldx, Rf,
+                                                                       NB, dinv, perm, rank, (float *)Q, ldq);
+    else
+      trsm32_wide_kernel<float><<<blocks, kT32Threads, 0, st>>>((const float *)X, m, (int)n, ldx, Rf, NB, dinv,
+                                                               perm, rank, (float *)Q, ldq);
+    return cudaGetLastError();
+  }
   if (prec == RCQR_BF16)
     return launch_trsm32_t<__nv_bfloat16>((const __nv_bfloat16 *)X, m, n, ldx, Rf, dinv, perm, rank,
                                           (float *)Q, ldq, NB, st);

@@ -132,28 +132,18 @@ size_t trsm_workspace(int64_t m, int64_t n, int prec) {
   return (prec != RCQR_F64 && trsm32_supported(n)) ? trsm32_workspace(n) : 0;
 }
 
-// FP64 X: row-wise substitution in FP64 (here).  FP32 / BF16 X (n <= 128): the
-// FP32 substitution of trsm_f32.cu, the working precision of the mixed path.
+// FP64 X: row-wise substitution in FP64 (here).  FP32 / BF16 X: the FP32
+// substitution of trsm_f32.cu, the working precision of the mixed path.
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
                         void *Q, int64_t ldq, Workspace &ws, cudaStream_t st, int *dev_status) {
   (void)dev_status;
   if (prec != RCQR_F64 && trsm32_supported(n))
     return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st);
+  if (prec != RCQR_F64) return cudaErrorInvalidValue;   // n <= 256 always takes the FP32 kernels
   const unsigned blocks = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
-  switch (prec) {
-    case RCQR_F64:
-      trsm_rows_kernel<double, double><<<blocks, kTrsmThreads, 0, st>>>(
-          (const double *)X, m, (int)n, ldx, R, ldr, perm, rank, (double *)Q, ldq);
-      break;
-    case RCQR_F32:
-      trsm_rows_kernel<float, float><<<blocks, kTrsmThreads, 0, st>>>(
-          (const float *)X, m, (int)n, ldx, R, ldr, perm, rank, (float *)Q, ldq);
-      break;
-    default:
-      trsm_rows_kernel<__nv_bfloat16, float><<<blocks, kTrsmThreads, 0, st>>>(
-          (const __nv_bfloat16 *)X, m, (int)n, ldx, R, ldr, perm, rank, (float *)Q, ldq);
-  }
+  trsm_rows_kernel<double, double><<<blocks, kTrsmThreads, 0, st>>>((const double *)X, m, (int)n, ldx, R, ldr,
+                                                                     perm, rank, (double *)Q, ldq);
   return cudaGetLastError();
 }
 

@@ -179,7 +179,8 @@ def test_chol_update_parity_and_failure(rc, inputs):
 # ----------------------------------------------------------------------------- bulk kernels
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("m,n,cond", [(1000, 1, 1.0), (4099, 17, 1e4), (20011, 64, 1e8), (3000, 200, 1e3)])
+@pytest.mark.parametrize("m,n,cond", [(1000, 1, 1.0), (4099, 17, 1e4), (20011, 64, 1e8), (3000, 200, 1e3),
+                                      (2001, 100, 1e4), (5003, 256, 1e3)])
 def test_trsm_parity(rc, inputs, prec, m, n, cond):
     X = inputs.svd_matrix(m, n, cond, 31 + n, dtype=prec, device=DEV)
     Rm = inputs.svd_matrix(4 * n, n, cond, 77, dtype="f64", device="cpu").numpy()
