@@ -4,11 +4,19 @@
 //
 // The problems are sorted by size (largest first) and dealt round-robin to a
 // set of library-owned streams forked from the caller's stream by an event
-// and joined back by events (under capture: a multi-branch graph).  Each
-// problem i runs the factorization of rcqr_factor with Theta's Philox stream
-// index i, in its stream's slice of the workspace.  rcqr_tune_batched times
-// the batch for several stream counts and keeps the fastest per device (and
-// in the JSON file named by RCQR_TUNE_CACHE, when set).
+// and joined back by events (under capture: a multi-branch graph).  Problem i
+// uses Theta's Philox stream index i.
+//
+// The direct variants run rcqr_factor's steps per problem in its stream's
+// slice of the workspace.  The rank-revealing variants run in three phases,
+// because their column-pivoted QR (one CTA, FP64, latency-bound) would
+// otherwise run at most one per stream: (A) every problem's status reset,
+// column norms and sketch, on the streams, into a per-problem region of the
+// workspace; (B) all the QRCPs, one CTA each, in launches of up to
+// kQrcpJobsPerLaunch problems spread over the streams; (C) every problem's
+// substitution (and, for RR2, the CholeskyQR pass), on the streams.
+// rcqr_tune_batched times the batch for several stream counts and keeps the
+// fastest per device (and in the JSON file named by RCQR_TUNE_CACHE, when set).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,6 +90,21 @@ bool valid_problem(const rcqr_problem &p, int variant, int prec) {
   return true;
 }
 
+bool rank_revealing(int variant) { return variant == RCQR_RR || variant == RCQR_RR2; }
+
+// Per-problem region of the rank-revealing phases: P (k x n), the squared column
+// norms (n) and the QRCP working copy, each 256-byte aligned.
+size_t rr_region_bytes(const rcqr_problem &p) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al((size_t)p.k * p.n * 8) + al((size_t)p.n * 8) + al(qrcp_work_doubles(p.k, p.n) * 8);
+}
+
+size_t rr_persist_bytes(const rcqr_problem *probs, int count) {
+  size_t s = 0;
+  for (int i = 0; i < count; ++i) s += rr_region_bytes(probs[i]);
+  return s;
+}
+
 size_t slice_bytes(const rcqr_problem *probs, int count, int variant, int prec) {
   size_t s = 0;
   for (int i = 0; i < count; ++i)
@@ -89,17 +112,120 @@ size_t slice_bytes(const rcqr_problem *probs, int count, int variant, int prec) 
   return (s + 255) & ~size_t(255);
 }
 
+rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int prec, double tau, void *workspace,
+                         size_t ws_bytes, cudaStream_t stream, int ns, DevStreams *d, const std::vector<int> &order) {
+  const size_t slice = slice_bytes(probs, count, variant, prec);
+  const size_t persist = rr_persist_bytes(probs, count);
+  if (persist + (size_t)ns * slice > ws_bytes) return RCQR_EWORKSPACE;
+  char *base = static_cast<char *>(workspace);
+  char *slices = base + persist;
+  std::vector<double *> Pp(count), cnp(count), gwp(count);
+  {
+    size_t off = 0;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    for (int i = 0; i < count; ++i) {
+      const rcqr_problem &p = probs[i];
+      Pp[i] = reinterpret_cast<double *>(base + off);
+      off += al((size_t)p.k * p.n * 8);
+      cnp[i] = reinterpret_cast<double *>(base + off);
+      off += al((size_t)p.n * 8);
+      gwp[i] = reinterpret_cast<double *>(base + off);
+      off += al(qrcp_work_doubles(p.k, p.n) * 8);
+    }
+  }
+  auto fork = [&](int nstreams) -> bool {
+    if (cudaEventRecord(d->fork, stream) != cudaSuccess) return false;
+    for (int s2 = 0; s2 < nstreams; ++s2)
+      if (cudaStreamWaitEvent(d->s[s2], d->fork, 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&](int nstreams) -> bool {
+    for (int s2 = 0; s2 < nstreams; ++s2) {
+      if (cudaEventRecord(d->join[s2], d->s[s2]) != cudaSuccess) return false;
+      if (cudaStreamWaitEvent(stream, d->join[s2], 0) != cudaSuccess) return false;
+    }
+    return true;
+  };
+  // (A) status, column norms and sketch
+  if (!fork(ns)) return RCQR_ECUDA;
+  for (int t = 0; t < count; ++t) {
+    const int i = order[t];
+    const rcqr_problem &p = probs[i];
+    cudaStream_t st = d->s[t % ns];
+    Workspace w(slices + (size_t)(t % ns) * slice, slice);
+    if (launch_reset_status(p.dev_status, st) != cudaSuccess) return RCQR_ECUDA;
+    if (launch_sketch(p.X, p.m, p.n, p.ldx, prec, p.k, p.seed, (uint32_t)i, 0, Pp[i], p.k, cnp[i], w, st,
+                      p.dev_status) != cudaSuccess)
+      return RCQR_ECUDA;
+  }
+  if (!join(ns)) return RCQR_ECUDA;
+  // (B) the QRCPs, one CTA each
+  const int nlaunch = (count + kQrcpJobsPerLaunch - 1) / kQrcpJobsPerLaunch;
+  const int nb = std::min(nlaunch, kMaxStreams);
+  if (!fork(nb)) return RCQR_ECUDA;
+  std::vector<QrcpJob> jobs(count);
+  for (int t = 0; t < count; ++t) {
+    const int i = order[t];
+    const rcqr_problem &p = probs[i];
+    jobs[t] = QrcpJob{Pp[i], (int)p.k, (int)p.n, p.k, cnp[i], p.R, p.ldr, p.perm, p.rank, p.dev_status, gwp[i]};
+  }
+  for (int c = 0; c < nlaunch; ++c) {
+    const int b0 = c * kQrcpJobsPerLaunch, cnt = std::min(kQrcpJobsPerLaunch, count - b0);
+    if (launch_qrcp_jobs(jobs.data() + b0, cnt, tau, d->s[c % nb]) != cudaSuccess) return RCQR_ECUDA;
+  }
+  if (!join(nb)) return RCQR_ECUDA;
+  // (C) substitution (Alg. 7 step 4) and, for RR2, one CholeskyQR pass (Alg. 3 steps 2-4)
+  const bool pass2 = variant == RCQR_RR2;
+  const int qprec = prec == RCQR_F64 ? RCQR_F64 : RCQR_F32;
+  if (!fork(ns)) return RCQR_ECUDA;
+  for (int t = 0; t < count; ++t) {
+    const int i = order[t];
+    const rcqr_problem &p = probs[i];
+    cudaStream_t st = d->s[t % ns];
+    Workspace w(slices + (size_t)(t % ns) * slice, slice);
+    double *A = w.take<double>((size_t)p.n * p.n);
+    double *Rp = w.take<double>((size_t)p.n * p.n);
+    if (!A || !Rp) return RCQR_EWORKSPACE;
+    const size_t mark = w.used;
+    auto scratch = [&]() -> Workspace & {
+      w.used = mark;
+      return w;
+    };
+    cudaError_t e;
+    const bool fused = pass2 && prec != RCQR_F64 && trsm32_gram_supported(p.n);
+    if (fused)
+      e = launch_trsm32_gram(p.X, p.m, p.n, p.ldx, prec, p.R, p.ldr, p.perm, p.rank, (float *)p.Q, p.ldq, A, p.n,
+                             scratch(), st);
+    else
+      e = launch_trsm(p.X, p.m, p.n, p.ldx, prec, p.R, p.ldr, p.perm, p.rank, p.Q, p.ldq, scratch(), st, p.dev_status);
+    if (e != cudaSuccess) return RCQR_ECUDA;
+    if (pass2) {
+      if (!fused && launch_gram(p.Q, p.m, p.n, p.ldq, qprec, p.rank, A, p.n, scratch(), st) != cudaSuccess)
+        return RCQR_ECUDA;
+      if (launch_chol_update(A, p.n, p.n, p.rank, Rp, p.n, p.R, p.ldr, p.dev_status, st) != cudaSuccess)
+        return RCQR_ECUDA;
+      if (launch_trsm(p.Q, p.m, p.n, p.ldq, qprec, Rp, p.n, nullptr, p.rank, p.Q, p.ldq, scratch(), st,
+                      p.dev_status) != cudaSuccess)
+        return RCQR_ECUDA;
+    }
+  }
+  if (!join(ns)) return RCQR_ECUDA;
+  return RCQR_OK;
+}
+
 rcqr_status run_batch(const rcqr_problem *probs, int count, int variant, int prec, double tau,
                       void *workspace, size_t ws_bytes, cudaStream_t stream, int ns) {
   DevStreams *d = nullptr;
   if (device_streams(&d) != cudaSuccess) return RCQR_ECUDA;
   const size_t slice = slice_bytes(probs, count, variant, prec);
-  if ((size_t)ns * slice > ws_bytes) return RCQR_EWORKSPACE;
+  if (!rank_revealing(variant) && (size_t)ns * slice > ws_bytes) return RCQR_EWORKSPACE;
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return probs[a].m * probs[a].n > probs[b].m * probs[b].n;
   });
+  if (rank_revealing(variant))
+    return run_batch_rr(probs, count, variant, prec, tau, workspace, ws_bytes, stream, ns, d, order);
   if (cudaEventRecord(d->fork, stream) != cudaSuccess) return RCQR_ECUDA;
   for (int s = 0; s < ns; ++s)
     if (cudaStreamWaitEvent(d->s[s], d->fork, 0) != cudaSuccess) return RCQR_ECUDA;
@@ -131,7 +257,8 @@ size_t rcqr_batched_workspace_size(const rcqr_problem *probs, int count, int var
   if (!probs || count < 1) return 0;
   for (int i = 0; i < count; ++i)
     if (rcqr_workspace_size(probs[i].m, probs[i].n, probs[i].k, variant, prec) == 0) return 0;
-  return (size_t)std::min(count, kMaxStreams) * slice_bytes(probs, count, variant, prec) + 256;
+  const size_t persist = rank_revealing(variant) ? rr_persist_bytes(probs, count) : 0;
+  return persist + (size_t)std::min(count, kMaxStreams) * slice_bytes(probs, count, variant, prec) + 256;
 }
 
 rcqr_status rcqr_factor_batched(const rcqr_problem *probs, int count, int variant, int prec, double tau,

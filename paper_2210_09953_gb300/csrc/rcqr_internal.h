@@ -93,6 +93,23 @@ cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, d
 cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
                         double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         int *dev_status, Workspace &ws, cudaStream_t st);
+// One QRCP of a batch (the arguments of launch_qrcp, gwork: qrcp_work_doubles(k, n) doubles).
+struct QrcpJob {
+  const double *P;
+  int k, n;
+  int64_t ldp;
+  const double *colnorm2;
+  double *R;
+  int64_t ldr;
+  int32_t *perm;
+  int64_t *rank;
+  int *status;
+  double *gwork;
+};
+constexpr int kQrcpJobsPerLaunch = 128;
+size_t qrcp_work_doubles(int64_t k, int64_t n);
+// Up to kQrcpJobsPerLaunch QRCPs in one launch, one CTA each.
+cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st);
 cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
                                double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status,
                                cudaStream_t st);

@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kSmallThreads = 256;
 constexpr size_t kSmemLimit = 200 * 1024;
+constexpr size_t kBatchedSmem = 96 * 1024;   // two batched QRCP CTAs per SM
 
 __device__ __forceinline__ int odd_ld(int rows) { return rows | 1; }
 
@@ -282,10 +283,9 @@ tsqr_pair_kernel(double *Rleaf, int n, int L, int stride) {
 }
 
 // Column-pivoted QR of P D^{-1} + rank + de-normalised R.
-__global__ void __launch_bounds__(kSmallThreads)
-qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
-            double tau, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
-            int *dev_status, double *gwork, int use_smem) {
+__device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
+                          double tau, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
+                          int *dev_status, double *gwork, int use_smem) {
   extern __shared__ double smem[];
   __shared__ double s_beta[256], s_diag[256], s_D[256], s_x[256], s_y[256], s_scal[4];
   __shared__ unsigned long long s_key[256];
@@ -428,6 +428,25 @@ qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const doubl
 // row j of R' with one thread per column.  The product R' R one 16-column
 // panel of R at a time through shared memory: column c of the new R depends
 // only on column c of the old one, so panels are overwritten in place.
+__global__ void __launch_bounds__(kSmallThreads)
+qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2, double tau, double *R,
+            int64_t ldr, int32_t *perm_out, int64_t *rank_out, int *dev_status, double *gwork, int use_smem) {
+  qrcp_body(P, k, n, ldp, colnorm2, tau, R, ldr, perm_out, rank_out, dev_status, gwork, use_smem);
+}
+
+// Many QRCPs in one launch (a batch of factorizations): CTA b runs job b, with its
+// working copy in shared memory when it fits the launch's allotment.
+struct QrcpJobs {
+  QrcpJob j[kQrcpJobsPerLaunch];
+};
+
+__global__ void __launch_bounds__(kSmallThreads)
+qrcp_batched_kernel(const __grid_constant__ QrcpJobs jobs, double tau, int64_t smem_doubles) {
+  const QrcpJob &jb = jobs.j[blockIdx.x];
+  const bool sm = (int64_t)odd_ld(jb.k) * jb.n <= smem_doubles;
+  qrcp_body(jb.P, jb.k, jb.n, jb.ldp, jb.colnorm2, tau, jb.R, jb.ldr, jb.perm, jb.rank, jb.status, jb.gwork, sm);
+}
+
 __global__ void __launch_bounds__(kSmallThreads)
 chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64_t *rank,
                    double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status) {
@@ -590,6 +609,26 @@ cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, cons
   if (sm) set_smem(qrcp_kernel, (int)kSmemLimit);
   qrcp_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, colnorm2, tau, R, ldr, perm,
                                                rank, dev_status, g, sm);
+  return cudaGetLastError();
+}
+
+size_t qrcp_work_doubles(int64_t k, int64_t n) { return (size_t)(k | 1) * n; }
+
+cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st) {
+  if (count < 1 || count > kQrcpJobsPerLaunch) return cudaErrorInvalidValue;
+  QrcpJobs pj;
+  int64_t need = 0;
+  for (int b = 0; b < count; ++b) {
+    pj.j[b] = jobs[b];
+    const int64_t d = (int64_t)(jobs[b].k | 1) * jobs[b].n;
+    if (d * 8 <= (int64_t)kBatchedSmem) need = std::max(need, d);
+  }
+  for (int b = count; b < kQrcpJobsPerLaunch; ++b) pj.j[b] = QrcpJob{};
+  if (need > 0) {
+    cudaError_t e = set_smem(qrcp_batched_kernel, (int)kBatchedSmem);
+    if (e != cudaSuccess) return e;
+  }
+  qrcp_batched_kernel<<<count, kSmallThreads, (size_t)need * 8, st>>>(pj, tau, need);
   return cudaGetLastError();
 }
 
