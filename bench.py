@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--m", type=int, default=M)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline oracle timing")
+    p.add_argument("--no-variants", action="store_true", help="skip the timings of the other variants and sizes")
     return p.parse_args()
 
 
@@ -155,6 +156,95 @@ def spectral_dev(G):
     import torch
     Gh = G.detach().cpu()
     return float(torch.linalg.matrix_norm(Gh - torch.eye(Gh.shape[0], dtype=Gh.dtype), ord=2))
+
+
+def conditioned(m, n, cond, seed, dtype, dev):
+    """X = G diag(sigma) V^T with G Gaussian (near-orthonormal columns for m >> n), sigma
+    log-spaced over cond, V orthonormal: condition number ~cond, built with one GEMM."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    G = torch.randn((m, n), dtype=torch.float32, device=dev, generator=g)
+    V, _ = torch.linalg.qr(torch.randn((n, n), dtype=torch.float64, generator=torch.Generator().manual_seed(seed)))
+    sigma = torch.logspace(0, -torch.log10(torch.tensor(float(cond))).item(), n, dtype=torch.float64)
+    B = (sigma[:, None] * V.T).to(torch.float32).to(dev)
+    X = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+    X.copy_(G @ B)
+    del G
+    return X if dtype == "f32" else X.to(torch.bfloat16).t().contiguous().t()
+
+
+def measure_variants(rc, inputs, timed, dev, X32, ws32, Q32):
+    """Time the other rows of the path: RCholeskyQR, the reduced variant, RRRCholeskyQR2,
+    16M x 128 FP32/BF16, 512 batched RR problems, the adjoint at 1M x 256."""
+    import torch
+    from paper_2210_09953_gb300 import autograd
+    out = {}
+    m = X32.shape[0]
+
+    def gbs(nbytes, ms):
+        return round(nbytes / (ms * 1e-3) / 1e9, 2)
+
+    ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT, Q=Q32, workspace=ws32), 5, 2)
+    out["rcholqr_mixed_4Mx64"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms)}
+    ms = timed(lambda: rc.rcqr_reduced(X32, K, SEED_THETA), 5, 2)
+    out["reduced_mixed_4Mx64"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms)}
+    ws_rr = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.RR2, rc.F32) + 256, dtype=torch.uint8, device=dev)
+    ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.RR2, tau=1e-5, Q=Q32, workspace=ws_rr), 5, 2)
+    _, _, _, rank, _ = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.RR2, tau=1e-5, Q=Q32, workspace=ws_rr)
+    out["rrrcholqr2_mixed_4Mx64_tau1e-5"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms), "rank": int(rank[0])}
+    del ws_rr
+
+    # configuration 3: 16,777,216 x 128, k = 512, RCholeskyQR2 (condition 1e8 by construction)
+    for prec in ("f32", "bf16"):
+        X = conditioned(1 << 24, 128, 1e8, 1003, prec, dev)
+        Q = rc.colmajor(1 << 24, 128, torch.float32, dev)
+        ws = torch.empty(rc.rcqr_workspace_size(1 << 24, 128, 512, rc.DIRECT2, rc.prec_of(X.dtype)) + 256,
+                         dtype=torch.uint8, device=dev)
+        ms = timed(lambda: rc.rcqr_factor(X, 512, 0x5EED0003, variant=rc.DIRECT2, Q=Q, workspace=ws), 3, 1)
+        G = Q.double().T @ Q.double()
+        orth = float(torch.linalg.matrix_norm(G.cpu() - torch.eye(128, dtype=torch.float64), ord=2))
+        out[f"rcholqr2_{prec}_16Mx128"] = {"ms": round(ms, 3), "GB/s": gbs(X.numel() * X.element_size(), ms),
+                                           "orth_QtQ_minus_I": orth}
+        del X, Q, ws, G
+        torch.cuda.empty_cache()
+
+    # configuration 4: 512 rank-deficient FP32 problems, one batched call replayed from a CUDA graph
+    shapes = inputs.batched_shapes(512, 1004)
+    Xs = [inputs.rank_deficient(mm, nn, nn // 2, 4000 + i, noise=1e-12, dtype="f32", device=dev)
+          for i, (mm, nn) in enumerate(shapes)]
+    b = rc.Batch(Xs, [4 * nn for _, nn in shapes], 0x5EED0004, rc.RR, 1e-5)
+    streams = b.tune()                  # the stream-count tuner, then capture with its choice
+    b.run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run()
+    ms = timed(graph.replay, 5, 2)
+    total = sum(mm * nn * 4 for mm, nn in shapes)
+    ok = bool((b.status[:, 0] == 0).all())
+    out["batched_rr_512"] = {"ms": round(ms, 3), "GB/s": gbs(total, ms), "problems": 512,
+                             "x_bytes": total, "cuda_graph": True, "tuned_streams": streams, "status_ok": ok}
+    del Xs, b, graph
+    torch.cuda.empty_cache()
+
+    # configuration 5: the adjoint, 1,048,576 x 256 FP32, k = 1024
+    X = conditioned(1 << 20, 256, 1e6, 1005, "f32", dev)
+    ms_f = timed(lambda: rc.rcqr_factor(X, 1024, 0xAD30, variant=rc.DIRECT2), 3, 1)
+    Xg = X.clone().requires_grad_(True)
+    W1 = torch.randn_like(X)
+    Qf, Rf = autograd.rcholqr2(Xg, 1024, 0xAD30)
+    loss = torch.sum(W1 * Qf) + torch.sum(Rf)
+
+    def backward():
+        Xg.grad = None
+        torch.autograd.grad(loss, Xg, retain_graph=True)
+    ms_b = timed(backward, 3, 1)
+    out["adjoint_rcholqr2_f32_1Mx256"] = {"forward_ms": round(ms_f, 3), "backward_ms": round(ms_b, 3),
+                                          "GB/s_forward": gbs(X.numel() * 4, ms_f)}
+    del X, Xg, W1, Qf, Rf, loss
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -313,6 +403,10 @@ def run_ours(args):
     ms_h2d = timed(lambda: Xf0.copy_(Xh_flat, non_blocking=True), 3, 1)
     ms_d2h = timed(lambda: Qh_flat.copy_(Qf0, non_blocking=True), 3, 1)
 
+    variants = None
+    if not args.no_variants and m == M:
+        variants = measure_variants(rc, inputs, timed, dev, X32, ws32, Q32)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -349,6 +443,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"orth_QtQ_minus_I": orth32, "residual_rel_F": res32, "status_ok": ok32},
             "fp64_path": fp64,
+            "variants": variants,
             "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4), "trsm_gram": round(ms_tg, 4)},
             "roofline": {"kernel": "trsm32_gram_kernel: Q = X R^-1 fused with A = Q^T Q (rcqr_trsm_gram, FP32 X)",
                          "bound": "alu", "achieved": round(tg_achieved, 3), "peak": round(alu_peak, 2),

@@ -63,14 +63,12 @@ cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int 
                           uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                           int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st,
                           int *dev_status = nullptr);
-// The exact tensor-core sketch (tcgen05): partial sums per CTA in the workspace.
+// The exact tensor-core sketch (tcgen05): partial sums per CTA in the workspace;
+// colnorm2 (nullable) receives the squared column norms from the same pass.
 size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec);
 cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                              uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
-                             int64_t ldp, int *dev_status, Workspace &ws, cudaStream_t st);
-// Squared column norms of X (matrix D^2 of Sec. 4), FP64.
-cudaError_t launch_colnorm2(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, double *out,
-                            Workspace &ws, cudaStream_t st);
+                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st);
 // The same sketch with its partial sums in a caller-given device buffer of
 // scratch_doubles doubles (fewer row groups when the buffer is small); no workspace.
 cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,

@@ -221,41 +221,18 @@ int sketch_groups(int64_t m, int64_t n, int64_t k, int64_t row_offset) {
 size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   Workspace w(nullptr, 0);
   w.take<char>(sketch_tc_workspace(m, n, k, row_offset, prec));
-  w.take<double>((size_t)colnorm_groups(m) * n);
   return w.used;
 }
 
-cudaError_t launch_colnorm2(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, double *out,
-                            Workspace &ws, cudaStream_t st) {
-  const int cg = colnorm_groups(m);
-  double *cp = ws.take<double>((size_t)cg * n);
-  if (!cp) return cudaErrorMemoryAllocation;
-  switch (prec) {
-    case RCQR_F64:
-      colnorm_partial_kernel<double><<<cg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, cg, cp);
-      break;
-    case RCQR_F32:
-      colnorm_partial_kernel<float><<<cg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, cg, cp);
-      break;
-    default:
-      colnorm_partial_kernel<__nv_bfloat16><<<cg, 256, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n,
-                                                                ldx, cg, cp);
-  }
-  colnorm_reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cp, cg, (int)n, out);
-  return cudaGetLastError();
-}
-
 // The sketch of the factorization path: the exact tensor-core kernel
-// (sketch_tc.cu) plus, for the rank-revealing variant, the column norms.
+// (sketch_tc.cu), whose exponent pre-pass also yields the column norms of the
+// rank-revealing variant.
 cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                           uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                           int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st,
                           int *dev_status) {
-  cudaError_t e = launch_sketch_tc(X, m, n, ldx, prec, k, seed, stream_id, row_offset, P, ldp,
-                                   dev_status, ws, st);
-  if (e != cudaSuccess) return e;
-  if (colnorm2) return launch_colnorm2(X, m, n, ldx, prec, colnorm2, ws, st);
-  return cudaSuccess;
+  return launch_sketch_tc(X, m, n, ldx, prec, k, seed, stream_id, row_offset, P, ldp, colnorm2, dev_status, ws,
+                          st);
 }
 
 cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,

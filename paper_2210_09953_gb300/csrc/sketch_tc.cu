@@ -487,12 +487,15 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Column exponents of every block of br rows: eblk[(blk - blk0) * n + j].  One
-// warp per (block, column), 8 per CTA; the rows outside [0, m) are skipped.
-template <class T>
+// Column exponents of every block of br rows: eblk[(blk - blk0) * n + j], and
+// (NORMS) the block's column sums of squares in FP64, ss[(blk - blk0) * n + j]
+// -- the squared column norms of Sec. 4's normalisation come from the same
+// pass over X.  One warp per (block, column), 8 per CTA; the rows outside
+// [0, m) are skipped.
+template <class T, bool NORMS>
 __global__ void __launch_bounds__(256) block_exp_kernel(const T *__restrict__ X, int64_t m, int n, int64_t ldx,
                                                         int64_t row_offset, int64_t blk0, int64_t nblk, int br,
-                                                        int *__restrict__ eblk) {
+                                                        int *__restrict__ eblk, double *__restrict__ ss) {
   const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= nblk * n) return;
@@ -501,13 +504,35 @@ __global__ void __launch_bounds__(256) block_exp_kernel(const T *__restrict__ X,
   const int64_t lr0 = (blk0 + bl) * br - row_offset;
   const T *col = X + (int64_t)j * ldx;
   decltype(mag_bits(T(0))) mx = 0;
+  double s2 = 0.0;
   for (int r = lane; r < br; r += 32) {
     const int64_t lr = lr0 + r;
-    if (lr >= 0 && lr < m) mx = max(mx, mag_bits(__ldg(col + lr)));
+    if (lr >= 0 && lr < m) {
+      const T v = __ldg(col + lr);
+      mx = max(mx, mag_bits(v));
+      if constexpr (NORMS) {
+        const double d = to_f64(v);
+        s2 = fma(d, d, s2);
+      }
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) eblk[w] = block_exp(mx);
+  if constexpr (NORMS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) ss[w] = s2;
+  }
+}
+
+// colnorm2[j] = sum over blocks of ss[b * n + j]: one warp per column, fixed order.
+__global__ void block_norms_reduce_kernel(const double *__restrict__ ss, int64_t nblk, int n,
+                                          double *__restrict__ colnorm2) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n) return;
+  const double s = warp_sum_strided(ss + j, (int)nblk, (int64_t)n);
+  if ((threadIdx.x & 31) == 0) colnorm2[j] = s;
 }
 
 template <int PREC, int KCH, int JCH>
@@ -799,12 +824,13 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, 
   w.take<double>((size_t)p.groups * n * k);
   w.take<long long>(acc64_count(p));
   w.take<int>((size_t)p.nblk * n);
+  w.take<double>((size_t)p.nblk * n);
   return w.used;
 }
 
 cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                              uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
-                             int64_t ldp, int *dev_status, Workspace &ws, cudaStream_t st) {
+                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st) {
   static bool table_ready[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -817,7 +843,8 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   double *partial = ws.take<double>((size_t)p.groups * n * k);
   long long *acc64 = ws.take<long long>(acc64_count(p));
   int *eblk = ws.take<int>((size_t)p.nblk * n);
-  if (!partial || !acc64 || !eblk) return cudaErrorMemoryAllocation;
+  double *ss = ws.take<double>((size_t)p.nblk * n);
+  if (!partial || !acc64 || !eblk || !ss) return cudaErrorMemoryAllocation;
   TcArgs a;
   a.X = X;
   a.m = m;
@@ -846,19 +873,21 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   cudaError_t e;
   {
     const unsigned eg = (unsigned)((p.nblk * n + 7) / 8);
+#define RCQR_BEXP(TT)                                                                                             \
+  if (colnorm2)                                                                                                   \
+    block_exp_kernel<TT, true><<<eg, 256, 0, st>>>((const TT *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk, p.BR, \
+                                                   eblk, ss);                                                    \
+  else                                                                                                            \
+    block_exp_kernel<TT, false><<<eg, 256, 0, st>>>((const TT *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk,      \
+                                                    p.BR, eblk, nullptr);
     switch (prec) {
-      case RCQR_F64:
-        block_exp_kernel<double><<<eg, 256, 0, st>>>((const double *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk,
-                                                      p.BR, eblk);
-        break;
-      case RCQR_F32:
-        block_exp_kernel<float><<<eg, 256, 0, st>>>((const float *)X, m, (int)n, ldx, row_offset, p.blk0, p.nblk,
-                                                     p.BR, eblk);
-        break;
-      default:
-        block_exp_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>((const __nv_bfloat16 *)X, m, (int)n, ldx, row_offset,
-                                                            p.blk0, p.nblk, p.BR, eblk);
+      case RCQR_F64: RCQR_BEXP(double) break;
+      case RCQR_F32: RCQR_BEXP(float) break;
+      default: RCQR_BEXP(__nv_bfloat16)
     }
+#undef RCQR_BEXP
+    if (colnorm2)
+      block_norms_reduce_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(ss, p.nblk, (int)n, colnorm2);
   }
   switch (prec) {
     case RCQR_F64: e = launch_tc_prec<RCQR_F64>(a, p, grid, st); break;

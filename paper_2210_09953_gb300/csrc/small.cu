@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kSmallThreads = 256;
 constexpr size_t kSmemLimit = 200 * 1024;
-constexpr size_t kBatchedSmem = 96 * 1024;   // two batched QRCP CTAs per SM
+constexpr size_t kBatchedSmem = kSmemLimit;   // one batched QRCP CTA per SM (<= 128 per launch)
 
 __device__ __forceinline__ int odd_ld(int rows) { return rows | 1; }
 
