@@ -282,6 +282,143 @@ tsqr_pair_kernel(double *Rleaf, int n, int L, int stride) {
   fold_triangles(Rleaf + t * n * n, Rleaf + u * n * n, n, n, scal);
 }
 
+// ---- R only on a cluster of 8 CTAs (k <= 32 RPL rows, n <= 64 CPW columns).
+// Householder QR distributed by columns: column g lives in the registers of one
+// warp (CTA g % 8, warp (g / 8) % 8, slot g / 64), lane l holding rows l, l + 32,
+// ...  Step j: every warp applies reflector j (read from its own shared memory)
+// to its columns > j; the warp that owns column j + 1 then forms reflector
+// j + 1 and stores it into the shared memory of all eight CTAs (distributed
+// shared memory), and one cluster barrier publishes it.  The reflector buffers
+// alternate between two slots, so one barrier per column suffices: a slot is
+// rewritten only after every CTA has passed the barrier that followed its
+// last read.  The trailing updates of a step run on eight SMs at once and the
+// chain of dependent operations per column (dot, update, norm, square root) is
+// one warp's.  Same reflections and the same diag(R) >= 0 convention as the
+// one-CTA kernels.
+constexpr int kClusterQR = 8;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t map_shared(const void *p, uint32_t rank) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p)), remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  return remote;
+}
+
+__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int RPL, int CPW>
+__global__ void __cluster_dims__(kClusterQR, 1, 1) __launch_bounds__(kSmallThreads)
+cluster_r_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double *R, int64_t ldr) {
+  __shared__ double vbuf[2][32 * RPL];
+  __shared__ double s_beta[64 * CPW], s_diag[64 * CPW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t crank = cluster_rank();
+  double a[CPW][RPL];
+  int g[CPW];
+#pragma unroll
+  for (int s = 0; s < CPW; ++s) {
+    g[s] = (int)crank + kClusterQR * (warp + 8 * s);
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      a[s][t] = (g[s] < n && row < k) ? P[row + (int64_t)g[s] * ldp] : 0.0;
+    }
+  }
+  uint32_t rv[kClusterQR];
+#pragma unroll
+  for (int c = 0; c < kClusterQR; ++c) rv[c] = map_shared(&vbuf[0][0], c);
+  // Reflector of column jj from slot s's registers: v = [0 .. 0, v0, a(jj+1:)],
+  // beta = 2 / v^T v, diag = -sign(x0) ||a(jj:)||; stored into every CTA's slot jj & 1.
+  auto reflect = [&](int s, int jj) {
+    double t = 0.0, x0 = 0.0;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const int row = lane + 32 * u;
+      if (row > jj) t = fma(a[s][u], a[s][u], t);
+      if (row == jj) x0 = a[s][u];
+    }
+    t = warp_allsum(t);
+    x0 = __shfl_sync(0xffffffffu, x0, jj & 31);
+    double beta = 0.0, d = 0.0, v0 = x0;
+    const double sigma = fma(x0, x0, t);
+    if (sigma > 0.0) {
+      const double alpha = sqrt(sigma);
+      const double sg = x0 >= 0.0 ? 1.0 : -1.0;
+      v0 = x0 + sg * alpha;
+      beta = 2.0 / fma(v0, v0, t);
+      d = -sg * alpha;
+    }
+    const uint32_t off = (uint32_t)((jj & 1) * 32 * RPL) * 8u;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const int row = lane + 32 * u;
+      const double v = row < jj ? 0.0 : (row == jj ? v0 : a[s][u]);
+#pragma unroll
+      for (int c = 0; c < kClusterQR; ++c) st_cluster_f64(rv[c] + off + (uint32_t)row * 8u, v);
+    }
+    if (lane < kClusterQR) {
+      st_cluster_f64(map_shared(&s_beta[jj], lane), beta);
+      st_cluster_f64(map_shared(&s_diag[jj], lane), d);
+    }
+  };
+  cluster_barrier();   // every CTA of the cluster is running before the first remote store
+  if (crank == 0 && warp == 0) reflect(0, 0);
+  cluster_barrier();
+  for (int j = 0; j < n; ++j) {
+    const double *v = vbuf[j & 1];
+    const double beta = s_beta[j];
+#pragma unroll
+    for (int s = 0; s < CPW; ++s) {
+      if (g[s] > j && g[s] < n) {   // warp-uniform
+        if (beta != 0.0) {
+          double w = 0.0;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) w = fma(v[lane + 32 * u], a[s][u], w);
+          const double bw = beta * warp_allsum(w);
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) a[s][u] = fma(-bw, v[lane + 32 * u], a[s][u]);
+        }
+        if (g[s] == j + 1) reflect(s, j + 1);
+      }
+    }
+    cluster_barrier();
+  }
+  // R = diag(sign d) * (upper triangle; diagonal d)
+#pragma unroll
+  for (int s = 0; s < CPW; ++s) {
+    if (g[s] < n) {
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int row = lane + 32 * u;
+        if (row < n) {
+          const double sg = s_diag[row < g[s] ? row : g[s]] < 0.0 ? -1.0 : 1.0;
+          double val = 0.0;
+          if (row < g[s]) val = sg * a[s][u];
+          else if (row == g[s]) val = sg * s_diag[row];
+          R[row + (int64_t)g[s] * ldr] = val;
+        }
+      }
+    }
+  }
+}
+
 // Column-pivoted QR of P D^{-1} + rank + de-normalised R.
 __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
                           double tau, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
@@ -423,11 +560,6 @@ __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ld
   }
 }
 
-// R' = chol(A[:r,:r]); R[:r, :] <- R' R[:r, :].
-// Left-looking Cholesky: the pivot of row j by warp 0 (one reciprocal), then
-// row j of R' with one thread per column.  The product R' R one 16-column
-// panel of R at a time through shared memory: column c of the new R depends
-// only on column c of the old one, so panels are overwritten in place.
 __global__ void __launch_bounds__(kSmallThreads)
 qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2, double tau, double *R,
             int64_t ldr, int32_t *perm_out, int64_t *rank_out, int *dev_status, double *gwork, int use_smem) {
@@ -447,46 +579,52 @@ qrcp_batched_kernel(const __grid_constant__ QrcpJobs jobs, double tau, int64_t s
   qrcp_body(jb.P, jb.k, jb.n, jb.ldp, jb.colnorm2, tau, jb.R, jb.ldr, jb.perm, jb.rank, jb.status, jb.gwork, sm);
 }
 
+// R' = chol(A[:r,:r]); R[:r, :] <- R' R[:r, :].
+// Left-looking Cholesky on a shared-memory copy of R' (odd leading dimension)
+// when it fits: step j forms, four threads per column, the dots of column j of
+// R' with columns j..r-1 over rows 0..j-1 -- column j's own dot gives the pivot
+// -- and after one barrier every thread finishes its entry of row j with the
+// pivot, which it recomputes itself (no serial broadcast step).  The product
+// R' R then reads R' from shared memory, one 16-column panel of R at a time:
+// column c of the new R depends only on column c of the old one, so panels are
+// overwritten in place.
+constexpr size_t kCholSmem = 160 * 1024;
+
 __global__ void __launch_bounds__(kSmallThreads)
 chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64_t *rank,
-                   double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status) {
+                   double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status, int use_smem) {
+  extern __shared__ double smem[];
   __shared__ double panel[256 * 16];
-  __shared__ double s_scal[2];
+  __shared__ double s_dot[256];
   __shared__ int s_fail;
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
+  const int64_t ldw = use_smem ? (n | 1) : ldrp;
+  double *W = use_smem ? smem : Rp;
   if (threadIdx.x == 0) s_fail = -1;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rp[(e % n) + (int64_t)(e / n) * ldrp] = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) W[(e % n) + (int64_t)(e / n) * ldw] = 0.0;
   __syncthreads();
+  const int q = threadIdx.x & 3, nq = blockDim.x >> 2;
   for (int j = 0; j < r; ++j) {
-    const double *cj = Rp + (int64_t)j * ldrp;
-    if (threadIdx.x < 32) {
-      double t = 0.0;
-      for (int i = threadIdx.x; i < j; i += 32) t = fma(cj[i], cj[i], t);
-      t = warp0_sum(t);
-      if (threadIdx.x == 0) {
-        const double d = A[j + (int64_t)j * lda] - t;
-        if (!(d > 0.0)) {
-          s_fail = j;
-        } else {
-          const double djj = sqrt(d);
-          Rp[j + (int64_t)j * ldrp] = djj;
-          s_scal[0] = 1.0 / djj;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_fail >= 0) break;
-    const double inv = s_scal[0];
-    const int q = threadIdx.x & 3, nq = blockDim.x >> 2;
-    for (int c0 = j + 1; c0 < r; c0 += nq) {
+    const double *cj = W + (int64_t)j * ldw;
+    for (int c0 = j; c0 < r; c0 += nq) {
       const int c = c0 + (threadIdx.x >> 2);
       const bool valid = c < r;
-      const double *cc = Rp + (int64_t)(valid ? c : j) * ldrp;
-      const double dot = quad_dot(cj, cc, 0, valid ? j : 0, q);
-      if (valid && q == 0) Rp[j + (int64_t)c * ldrp] = (A[j + (int64_t)c * lda] - dot) * inv;
+      const double dot = quad_dot(cj, W + (int64_t)(valid ? c : j) * ldw, 0, valid ? j : 0, q);
+      if (valid && q == 0) s_dot[c] = dot;
     }
     __syncthreads();
+    const double d = A[j + (int64_t)j * lda] - s_dot[j];   // the same value in every thread
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) s_fail = j;
+      break;
+    }
+    const double djj = sqrt(d);
+    for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x)
+      W[j + (int64_t)c * ldw] = (A[j + (int64_t)c * lda] - s_dot[c]) / djj;
+    if (threadIdx.x == 0) W[j + (int64_t)j * ldw] = djj;
+    __syncthreads();
   }
+  __syncthreads();
   if (s_fail >= 0) {
     if (threadIdx.x == 0 && dev_status) {
       dev_status[0] = RCQR_ENOTSPD;
@@ -494,6 +632,9 @@ chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64
     }
     return;
   }
+  if (use_smem)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+      Rp[(e % n) + (int64_t)(e / n) * ldrp] = W[(e % n) + (int64_t)(e / n) * ldw];
   for (int c0 = 0; c0 < n; c0 += 16) {
     const int cw = min(16, n - c0);
     for (int e = threadIdx.x; e < r * cw; e += blockDim.x) {
@@ -506,7 +647,7 @@ chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64
       const int cg = c0 + c;
       const int lend = min(cg, r - 1);
       double s = 0.0;
-      for (int l = i; l <= lend; ++l) s = fma(Rp[i + (int64_t)l * ldrp], panel[c * 256 + l], s);
+      for (int l = i; l <= lend; ++l) s = fma(W[i + (int64_t)l * ldw], panel[c * 256 + l], s);
       R[i + (int64_t)cg * ldr] = (cg >= i) ? s : 0.0;
     }
     __syncthreads();
@@ -551,6 +692,10 @@ int tsqr_leaves(int64_t k, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(k / n, 32));
 }
 
+// The cluster kernel covers the sketches of up to 512 rows and 128 columns
+// (k <= 4n there, the shapes whose one-CTA Householder is FP64-throughput bound).
+bool cluster_r_supported(int64_t k, int64_t n) { return n <= 128 && k <= 512 && k >= n; }
+
 }  // namespace
 
 size_t small_qr_workspace(int64_t k, int64_t n) {
@@ -563,6 +708,24 @@ size_t small_qr_workspace(int64_t k, int64_t n) {
 
 cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, double *R, int64_t ldr,
                            Workspace &ws, cudaStream_t st) {
+  if (cluster_r_supported(k, n)) {
+    const int rpl = k <= 64 ? 2 : (k <= 128 ? 4 : (k <= 256 ? 8 : 16));
+#define RCQR_CLUSTER_R(RP)                                                                           \
+  case RP:                                                                                           \
+    if (n <= 64)                                                                                     \
+      cluster_r_kernel<RP, 1><<<kClusterQR, kSmallThreads, 0, st>>>(P, (int)k, (int)n, ldp, R, ldr); \
+    else                                                                                             \
+      cluster_r_kernel<RP, 2><<<kClusterQR, kSmallThreads, 0, st>>>(P, (int)k, (int)n, ldp, R, ldr); \
+    break;
+    switch (rpl) {
+      RCQR_CLUSTER_R(2)
+      RCQR_CLUSTER_R(4)
+      RCQR_CLUSTER_R(8)
+      RCQR_CLUSTER_R(16)
+    }
+#undef RCQR_CLUSTER_R
+    return cudaGetLastError();
+  }
   const int L = tsqr_leaves(k, n);
   double *g = ws.take<double>((size_t)((k + L) | 1) * n + (size_t)2 * L * n);
   double *Rleaf = ws.take<double>((size_t)L * n * n);
@@ -635,7 +798,14 @@ cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStr
 cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
                                double *Rp, int64_t ldrp, double *R, int64_t ldr,
                                int *dev_status, cudaStream_t st) {
-  chol_update_kernel<<<1, kSmallThreads, 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, R, ldr, dev_status);
+  const size_t bytes = (size_t)(n | 1) * n * 8;
+  const bool sm = bytes <= kCholSmem;
+  if (sm) {
+    cudaError_t e = set_smem(chol_update_kernel, (int)kCholSmem);
+    if (e != cudaSuccess) return e;
+  }
+  chol_update_kernel<<<1, kSmallThreads, sm ? bytes : 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, R, ldr, dev_status,
+                                                              sm);
   return cudaGetLastError();
 }
 

@@ -118,9 +118,11 @@ def test_small_qr_parity(rc, inputs, k, n, cond):
 
 
 @pytest.mark.parametrize("k,n,cond", [(8, 1, 1.0), (72, 16, 1e4), (256, 64, 1e8), (520, 130, 1e10),
-                                      (263, 7, 1e12), (2048, 256, 1e3)])
+                                      (263, 7, 1e12), (2048, 256, 1e3), (300, 100, 1e6), (128, 128, 1e4),
+                                      (512, 65, 1e8), (2000, 40, 1e8)])
 def test_small_r_tree_parity(rc, inputs, k, n, cond):
-    # R without S: the TSQR tree (leaf Householder QRs, then folds of stacked triangles)
+    # R without S: the cluster kernel (k <= 512, n <= 128: columns spread over eight CTAs)
+    # or the TSQR tree (leaf Householder QRs, then folds of stacked triangles)
     P = inputs.svd_matrix(k, n, cond, 19 + n, dtype="f64", device=DEV)
     R = rc.rcqr_small_qr(P, want_S=False)
     torch.cuda.synchronize()
@@ -155,8 +157,8 @@ def test_qrcp_zero_sketch_reports_rank0(rc):
     assert int(rank[0]) == 0 and int(status[0]) == -3
 
 
-def test_chol_update_parity_and_failure(rc, inputs):
-    n = 40
+@pytest.mark.parametrize("n", [40, 128, 150])     # R' in shared memory up to n = 141, else in place
+def test_chol_update_parity_and_failure(rc, inputs, n):
     G = inputs.gaussian_colmajor(500, n, 3, device=DEV)
     A = (G.t() @ G).t().contiguous().t()           # column-major SPD
     R0 = torch.triu(torch.randn(n, n, dtype=torch.float64, device=DEV)).t().contiguous().t()
