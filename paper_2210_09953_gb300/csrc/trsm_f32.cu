@@ -186,12 +186,43 @@ trsm32_wide_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, cons
 // ---- Substitution fused with the Gram of the second pass (Alg. 2 step 3 and
 // Alg. 3 step 2, mixed path, NB <= 64).  A persistent CTA takes tiles of 256
 // rows: two rows per thread are substituted as in trsm32_kernel, written to Q
-// and to a shared tile, and the CTA's partial Q^T Q (thread (ti, tj): entries
-// (ti + 16a, tj + 8b)) is accumulated from the tile in 32-row FP32 chunks with
-// compensated chunk sums -- the arithmetic of gram32_kernel -- so Q is not read
-// back from memory.
+// and to a shared tile, and the CTA's partial Q^T Q is accumulated from the
+// tile in 32-row FP32 chunks with compensated chunk sums -- the arithmetic of
+// gram32_kernel -- so Q is not read back from memory.
+//
+// Only the upper triangle of Q^T Q is needed.  In 8-row strips (strip s: rows
+// 8s..8s+7, columns 8s..63), warp w takes strips w and 7 - w, whose widths add
+// up to 72 columns.  One code path serves all warps (the instruction cache
+// holds one copy): lane (p, c) owns rows 2p, 2p + 1 of both strips and columns
+// c + 8u of each, u < 8 in strip w and u < 4 in strip 7 - w; columns past 63
+// wrap to columns below the strip's diagonal block, computed but not stored.
+// That is 96 of the 128 multiply-adds per row and lane of the full product.
+// The tile is column-major with a stride of 4 words mod 32 banks, so each
+// operand load of a warp (8 distinct columns, or 4 distinct rows) is one
+// conflict-free wavefront.
 constexpr int kTGRows = 2 * kT32Threads;      // rows per tile
 constexpr int kTGStride = kTGRows + 4;        // tile column stride (16-byte aligned rows)
+constexpr int kTGG1 = 8, kTGG2 = 4;           // column groups per lane in the two strips
+constexpr int kTGG = kTGG1 + kTGG2;
+
+struct TgLane {
+  int arow[2][2];     // [strip][h]: tile column of the lane's rows
+  int bcol[kTGG];     // tile column of group u (strip 1: u < kTGG1)
+};
+
+__device__ __forceinline__ TgLane tg_lane(int w, int p, int c) {
+  TgLane L;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    L.arow[0][h] = 8 * w + 2 * p + h;
+    L.arow[1][h] = 8 * (7 - w) + 2 * p + h;
+  }
+#pragma unroll
+  for (int u = 0; u < kTGG1; ++u) L.bcol[u] = (8 * w + 8 * u + c) & 63;
+#pragma unroll
+  for (int u = 0; u < kTGG2; ++u) L.bcol[kTGG1 + u] = (8 * (7 - w) + 8 * u + c) & 63;
+  return L;
+}
 
 template <class TX, int NB>
 __global__ void __launch_bounds__(kT32Threads)
@@ -209,12 +240,12 @@ trsm32_gram_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, cons
   for (int e = tid; e < 64 * kTGStride; e += blockDim.x) Ts[e] = 0.0f;
   __syncthreads();
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
-  const int ti = tid & 15, tj = tid >> 4;
-  float outer[4][8], comp[4][8];
+  const TgLane L = tg_lane(tid >> 5, tid & 3, (tid >> 2) & 7);
+  float outer[2][kTGG], comp[2][kTGG];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) outer[a][b] = comp[a][b] = 0.0f;
+    for (int u = 0; u < kTGG; ++u) outer[h][u] = comp[h][u] = 0.0f;
   const int64_t tiles = (m + kTGRows - 1) / kTGRows;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kTGRows + tid;
@@ -265,50 +296,56 @@ trsm32_gram_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, cons
       }
     }
     __syncthreads();
-    // partial Gram of the tile: eight 32-row chunks, each summed in FP32 and added compensated
+    // partial Gram of the tile (upper triangle): eight 32-row chunks, each summed in FP32
+    // and added compensated
 #pragma unroll 1
     for (int c0 = 0; c0 < kTGRows; c0 += 32) {
-      float inner[4][8];
+      float inner[2][kTGG];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) inner[a][b] = 0.0f;
+        for (int u = 0; u < kTGG; ++u) inner[h][u] = 0.0f;
 #pragma unroll 2
       for (int s4 = 0; s4 < 8; ++s4) {
         const int rr = c0 + 4 * s4;
-        float4 va[4], vb[8];
+        float4 a[2][2], b[kTGG];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) va[a] = *reinterpret_cast<const float4 *>(Ts + (ti + 16 * a) * kTGStride + rr);
+        for (int st = 0; st < 2; ++st)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) vb[b] = *reinterpret_cast<const float4 *>(Ts + (tj + 8 * b) * kTGStride + rr);
+          for (int h = 0; h < 2; ++h) a[st][h] = *reinterpret_cast<const float4 *>(Ts + L.arow[st][h] * kTGStride + rr);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int u = 0; u < kTGG; ++u) b[u] = *reinterpret_cast<const float4 *>(Ts + L.bcol[u] * kTGStride + rr);
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            inner[a][b] = fmaf(va[a].x, vb[b].x, inner[a][b]);
-            inner[a][b] = fmaf(va[a].y, vb[b].y, inner[a][b]);
-            inner[a][b] = fmaf(va[a].z, vb[b].z, inner[a][b]);
-            inner[a][b] = fmaf(va[a].w, vb[b].w, inner[a][b]);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int u = 0; u < kTGG; ++u) {
+            const float4 av = a[u < kTGG1 ? 0 : 1][h];
+            inner[h][u] = fmaf(av.x, b[u].x, inner[h][u]);
+            inner[h][u] = fmaf(av.y, b[u].y, inner[h][u]);
+            inner[h][u] = fmaf(av.z, b[u].z, inner[h][u]);
+            inner[h][u] = fmaf(av.w, b[u].w, inner[h][u]);
           }
       }
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const float y = inner[a][b] - comp[a][b];
-          const float tt = outer[a][b] + y;
-          comp[a][b] = (tt - outer[a][b]) - y;
-          outer[a][b] = tt;
+        for (int u = 0; u < kTGG; ++u) {
+          const float y = inner[h][u] - comp[h][u];
+          const float tt = outer[h][u] + y;
+          comp[h][u] = (tt - outer[h][u]) - y;
+          outer[h][u] = tt;
         }
     }
     __syncthreads();   // the tile is rewritten by the next iteration
   }
+  // entries i <= j only: the reduction reads the upper triangle of every partial
+  double *pb = partial + (int64_t)blockIdx.x * n * n;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int i = ti + 16 * a, j = tj + 8 * b;
-      if (i < n && j < n) partial[((int64_t)blockIdx.x * n + j) * n + i] = (double)outer[a][b] - (double)comp[a][b];
+    for (int u = 0; u < kTGG; ++u) {
+      const int i = L.arow[u < kTGG1 ? 0 : 1][h], j = L.bcol[u];
+      if (i <= j && j < n) pb[(int64_t)j * n + i] = (double)outer[h][u] - (double)comp[h][u];
     }
 }
 
