@@ -31,10 +31,10 @@ ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (abou
 # DRAM bytes (read + write) of the three kernels of one rcqr_sketch call on the 4M x 64 FP32
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1M-row launch of each kernel,
 # scaled by 4 (per-row traffic is the same), profiles/sketch_call_dram_1Mx64.md.
-SKETCH_CALL_TRAFFIC = 4 * (268452608 + 3247872 + 288038912 + 25882112 + 19934720)
+SKETCH_CALL_TRAFFIC = 4 * (268455680 + 140288 + 287843584 + 25611264 + 19934208)
 # the same for trsm32_gram_kernel (X read once, Q written once; the writes still in L2 when
 # the kernel ends are not counted), profiles/sketch_call_dram_1Mx64.md
-TRSM_GRAM_TRAFFIC = 4 * (268790272 + 222318336)
+TRSM_GRAM_TRAFFIC = 4 * (268658432 + 218687488)
 
 
 def parse():

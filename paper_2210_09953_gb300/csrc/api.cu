@@ -287,9 +287,7 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   if (pass2) {
     // Alg. 3 steps 2-4 on the computed Q
     if (!fused) RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
-    RCQR_TRY(launch_chol_update(b.A, n, n, rkp, b.Rp, n, R, ldr, dev_status, stream));
-    RCQR_TRY(launch_trsm(Q, m, n, ldq, qprec, b.Rp, n, nullptr, rkp, Q, ldq, *scratch(), stream,
-                         dev_status));
+    RCQR_TRY(launch_cholqr_pass(b.A, n, rkp, b.Rp, R, ldr, Q, m, ldq, qprec, *scratch(), stream, dev_status));
   }
 #undef RCQR_TRY
   return RCQR_OK;

@@ -202,10 +202,8 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
     if (pass2) {
       if (!fused && launch_gram(p.Q, p.m, p.n, p.ldq, qprec, p.rank, A, p.n, scratch(), st) != cudaSuccess)
         return RCQR_ECUDA;
-      if (launch_chol_update(A, p.n, p.n, p.rank, Rp, p.n, p.R, p.ldr, p.dev_status, st) != cudaSuccess)
-        return RCQR_ECUDA;
-      if (launch_trsm(p.Q, p.m, p.n, p.ldq, qprec, Rp, p.n, nullptr, p.rank, p.Q, p.ldq, scratch(), st,
-                      p.dev_status) != cudaSuccess)
+      if (launch_cholqr_pass(A, p.n, p.rank, Rp, p.R, p.ldr, p.Q, p.m, p.ldq, qprec, scratch(), st,
+                             p.dev_status) != cudaSuccess)
         return RCQR_ECUDA;
     }
   }

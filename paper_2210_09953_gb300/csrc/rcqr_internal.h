@@ -108,9 +108,15 @@ constexpr int kQrcpJobsPerLaunch = 128;
 size_t qrcp_work_doubles(int64_t k, int64_t n);
 // Up to kQrcpJobsPerLaunch QRCPs in one launch, one CTA each.
 cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st);
+// R' = chol(A[:r,:r]), R[:r,:] <- R' R[:r,:].
 cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
                                double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status,
                                cudaStream_t st);
+// Alg. 3 steps 3-4: R' = chol(A), R <- R' R, Q <- Q R'^{-1} (in place).
+cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, double *Rp, double *R, int64_t ldr,
+                               void *Q, int64_t m, int64_t ldq, int qprec, Workspace &ws, cudaStream_t st,
+                               int *dev_status);
+
 // W = R^{-1} (n x n upper) for the leading rank x rank block (rank nullable).
 cudaError_t launch_tri_inverse(const double *R, int64_t n, int64_t ldr, const int64_t *rank,
                                double *W, int64_t ldw, cudaStream_t st);

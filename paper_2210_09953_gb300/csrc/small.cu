@@ -579,23 +579,22 @@ qrcp_batched_kernel(const __grid_constant__ QrcpJobs jobs, double tau, int64_t s
   qrcp_body(jb.P, jb.k, jb.n, jb.ldp, jb.colnorm2, tau, jb.R, jb.ldr, jb.perm, jb.rank, jb.status, jb.gwork, sm);
 }
 
-// R' = chol(A[:r,:r]); R[:r, :] <- R' R[:r, :].
-// Left-looking Cholesky on a shared-memory copy of R' (odd leading dimension)
-// when it fits: step j forms, four threads per column, the dots of column j of
-// R' with columns j..r-1 over rows 0..j-1 -- column j's own dot gives the pivot
-// -- and after one barrier every thread finishes its entry of row j with the
-// pivot, which it recomputes itself (no serial broadcast step).  The product
-// R' R then reads R' from shared memory, one 16-column panel of R at a time:
-// column c of the new R depends only on column c of the old one, so panels are
-// overwritten in place.
+// R' = chol(A[:r,:r]) (Alg. 3 step 3) on one CTA: left-looking on a shared-memory
+// copy of R' (odd leading dimension) when it fits.  Step j forms, four threads
+// per column, the dots of column j of R' with columns j..r-1 over rows 0..j-1;
+// one thread takes the pivot's square root and reciprocal (GB300's FP64 unit
+// runs a warp instruction in ~16 cycles, so redundant pivots in every thread
+// cost more than the barrier that broadcasts one), and row j is finished by
+// multiplication.  A failed pivot leaves R'_jj = 0, which the apply kernel
+// checks.  (R' only; the update R <- R' R is chol_apply_kernel.)
 constexpr size_t kCholSmem = 160 * 1024;
 
 __global__ void __launch_bounds__(kSmallThreads)
-chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64_t *rank,
-                   double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status, int use_smem) {
+chol_factor_kernel(const double *__restrict__ A, int n, int64_t lda, const int64_t *rank, double *Rp, int64_t ldrp,
+                   int *dev_status, int use_smem) {
   extern __shared__ double smem[];
-  __shared__ double panel[256 * 16];
   __shared__ double s_dot[256];
+  __shared__ double s_inv;
   __shared__ int s_fail;
   const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
   const int64_t ldw = use_smem ? (n | 1) : ldrp;
@@ -613,44 +612,81 @@ chol_update_kernel(const double *__restrict__ A, int n, int64_t lda, const int64
       if (valid && q == 0) s_dot[c] = dot;
     }
     __syncthreads();
-    const double d = A[j + (int64_t)j * lda] - s_dot[j];   // the same value in every thread
-    if (!(d > 0.0)) {
-      if (threadIdx.x == 0) s_fail = j;
-      break;
+    if (threadIdx.x == 0) {
+      const double d = A[j + (int64_t)j * lda] - s_dot[j];
+      if (!(d > 0.0)) {
+        s_fail = j;
+      } else {
+        const double djj = sqrt(d);
+        W[j + (int64_t)j * ldw] = djj;
+        s_inv = 1.0 / djj;
+      }
     }
-    const double djj = sqrt(d);
+    __syncthreads();
+    if (s_fail >= 0) break;
+    const double inv = s_inv;
     for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x)
-      W[j + (int64_t)c * ldw] = (A[j + (int64_t)c * lda] - s_dot[c]) / djj;
-    if (threadIdx.x == 0) W[j + (int64_t)j * ldw] = djj;
+      W[j + (int64_t)c * ldw] = (A[j + (int64_t)c * lda] - s_dot[c]) * inv;
     __syncthreads();
   }
-  __syncthreads();
   if (s_fail >= 0) {
     if (threadIdx.x == 0 && dev_status) {
       dev_status[0] = RCQR_ENOTSPD;
       dev_status[1] = s_fail;
     }
-    return;
   }
   if (use_smem)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x)
       Rp[(e % n) + (int64_t)(e / n) * ldrp] = W[(e % n) + (int64_t)(e / n) * ldw];
-  for (int c0 = 0; c0 < n; c0 += 16) {
-    const int cw = min(16, n - c0);
-    for (int e = threadIdx.x; e < r * cw; e += blockDim.x) {
-      const int i = e % r, c = e / r;
-      panel[c * 256 + i] = R[i + (int64_t)(c0 + c) * ldr];
+}
+
+// R[:r, c] <- R' R[:r, c] (Alg. 3 step 3's update of the first pass's R), one
+// CTA per column c: column c of the product depends only on column c of the
+// old R, so the columns are updated in place independently.  For n <= 64 the
+// block R'[0..c, 0..c] is staged in shared memory first, eight independent
+// loads per thread in flight (not one L2 round trip per element).  Nothing is
+// written if R' has a non-positive diagonal entry (a failed Cholesky).
+constexpr int kApplyThreads = 64;
+
+__global__ void __launch_bounds__(kApplyThreads)
+chol_apply_kernel(const double *__restrict__ Rp, int n, int64_t ldrp, const int64_t *rank, double *R, int64_t ldr) {
+  __shared__ double s_col[256];
+  __shared__ double s_R[64 * 65];     // R'[0..ce, 0..ce] (column stride 65), n <= 64
+  __shared__ int s_bad;
+  const int c = blockIdx.x;
+  const int r = rank ? (int)(*rank < (int64_t)n ? *rank : (int64_t)n) : n;
+  const bool staged = n <= 64;
+  const int ce = min(c, r - 1);       // last row / column of R' this column needs
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
+    if (!(Rp[i + (int64_t)i * ldrp] > 0.0)) s_bad = 1;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) s_col[i] = R[i + (int64_t)c * ldr];
+  if (staged && ce >= 0) {
+    const int cnt = (ce + 1) * (ce + 1);
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += 8 * blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < cnt ? Rp[(e % (ce + 1)) + (int64_t)(e / (ce + 1)) * ldrp] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < cnt) s_R[(e % (ce + 1)) + (e / (ce + 1)) * 65] = v[u];
+      }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < r * cw; e += blockDim.x) {
-      const int i = e % r, c = e / r;
-      const int cg = c0 + c;
-      const int lend = min(cg, r - 1);
-      double s = 0.0;
-      for (int l = i; l <= lend; ++l) s = fma(W[i + (int64_t)l * ldw], panel[c * 256 + l], s);
-      R[i + (int64_t)cg * ldr] = (cg >= i) ? s : 0.0;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (s_bad) return;   // R untouched
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    double s = 0.0;
+    if (staged)
+      for (int l = i; l <= ce; ++l) s = fma(s_R[i + l * 65], s_col[l], s);
+    else
+      for (int l = i; l <= ce; ++l) s = fma(Rp[i + (int64_t)l * ldrp], s_col[l], s);
+    R[i + (int64_t)c * ldr] = c >= i ? s : 0.0;
   }
 }
 
@@ -801,11 +837,11 @@ cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const in
   const size_t bytes = (size_t)(n | 1) * n * 8;
   const bool sm = bytes <= kCholSmem;
   if (sm) {
-    cudaError_t e = set_smem(chol_update_kernel, (int)kCholSmem);
+    cudaError_t e = set_smem(chol_factor_kernel, (int)kCholSmem);
     if (e != cudaSuccess) return e;
   }
-  chol_update_kernel<<<1, kSmallThreads, sm ? bytes : 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, R, ldr, dev_status,
-                                                              sm);
+  chol_factor_kernel<<<1, kSmallThreads, sm ? bytes : 0, st>>>(A, (int)n, lda, rank, Rp, ldrp, dev_status, sm);
+  chol_apply_kernel<<<(unsigned)n, kApplyThreads, 0, st>>>(Rp, (int)n, ldrp, rank, R, ldr);
   return cudaGetLastError();
 }
 

@@ -153,6 +153,16 @@ cudaError_t launch_gram_reduce(const double *partial, int groups, int64_t n, dou
   return cudaGetLastError();
 }
 
+// Alg. 3 steps 3-4 on a computed Q with Gram A: R' = chol(A), R <- R' R,
+// Q <- Q R'^{-1} by substitution (in place).
+cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, double *Rp, double *R, int64_t ldr,
+                               void *Q, int64_t m, int64_t ldq, int qprec, Workspace &ws, cudaStream_t st,
+                               int *dev_status) {
+  cudaError_t e = launch_chol_update(A, n, n, rank, Rp, n, R, ldr, dev_status, st);
+  if (e != cudaSuccess) return e;
+  return launch_trsm(Q, m, n, ldq, qprec, Rp, n, nullptr, rank, Q, ldq, ws, st, dev_status);
+}
+
 size_t gram_workspace(int64_t m, int64_t n) {
   Workspace w(nullptr, 0);
   w.take<double>((size_t)std::max(gram_groups(m, n), gram32_groups(m, n)) * n * n);
