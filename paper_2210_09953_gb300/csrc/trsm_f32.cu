@@ -95,12 +95,16 @@ trsm32_kernel(const TX *__restrict__ X, int64_t m, int n, int64_t ldx, const flo
 #pragma unroll
     for (int t = 0; t < RR; ++t) q[t][j] = s[t] * dj;
   }
+  // the store addresses are recomputed from an opaque copy of ldq rather than kept
+  // live from the loads (2 NB 64-bit addresses would cost 4 NB registers)
+  int64_t lds = ldq;
+  asm volatile("" : "+l"(lds));
 #pragma unroll
   for (int j = 0; j < NB; ++j)
     if (j < n)
 #pragma unroll
       for (int t = 0; t < RR; ++t)
-        if (live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * ldq] = q[t][j];
+        if (live[t]) Q[row0 + (int64_t)t * kT32Threads + (int64_t)j * lds] = q[t][j];
 }
 
 // ---- Wide R (64 < n <= 256): the row's columns in panels of 64.  A panel is
