@@ -26,6 +26,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M, N, K, COND = 4194304, 64, 256, 1e8
+METRIC = "GB/s of X factored (RCholeskyQR2, mixed path: FP32 X) at stated ||Q^TQ-I||"
+
+
+def workload_name(m):
+    return f"rcholqr2 {m}x{N} k={K} cond 1e8 (U diag(sigma) V^T), X f32 column-major"
+
+
 SEED_X, SEED_THETA = 1002, 0x5EED0002
 ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (about 10-20 s on 16 cores)
 # DRAM bytes (read + write) of the three kernels of one rcqr_sketch call on the 4M x 64 FP32
@@ -90,11 +97,11 @@ def run_reference(args):
         gbs, dt, _ = oracle_time(ORACLE_ROWS // 4)
         vals.append(gbs)
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": "GB/s of X factored (RCholeskyQR2, cond 1e8)", "value": round(v, 4),
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4),
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"rcholqr2 {args.m}x{N} f32-stored cond 1e8 k={K}", "sample_rows": ORACLE_ROWS // 4},
+            "config": {"workload": workload_name(args.m), "sample_rows": ORACLE_ROWS // 4},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"first {ORACLE_ROWS // 4} rows per step"},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -433,12 +440,12 @@ def run_ours(args):
         if not args.no_cpu:
             cpu = cpu_baseline_record(ORACLE_ROWS)
         line = {
-            "metric": "GB/s of X factored (RCholeskyQR2, mixed path: FP32 X) at stated ||Q^TQ-I||",
+            "metric": METRIC,
             "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms32, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 storage / f64 sketch and small ops",
             "data": "synthetic",
-            "config": {"workload": f"rcholqr2 {m}x{N} k={K} cond 1e8 (U diag(sigma) V^T), X f32 column-major",
+            "config": {"workload": workload_name(m),
                        "seed_theta": SEED_THETA, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"orth_QtQ_minus_I": orth32, "residual_rel_F": res32, "status_ok": ok32},
