@@ -37,10 +37,10 @@ SEED_X, SEED_THETA = 1002, 0x5EED0002
 ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (about 10-20 s on 16 cores)
 # DRAM bytes (read + write) of the three kernels of one rcqr_sketch call on the 4M x 64 FP32
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1M-row launch of each kernel,
-# scaled by 4 (per-row traffic is the same), profiles/sketch_call_dram_1Mx64.md.
+# scaled by 4 (per-row traffic is the same).
 SKETCH_CALL_TRAFFIC = 4 * (268455680 + 140288 + 287843584 + 25611264 + 19934208)
 # the same for trsm32_gram_kernel (X read once, Q written once; the writes still in L2 when
-# the kernel ends are not counted), profiles/sketch_call_dram_1Mx64.md
+# the kernel ends are not counted)
 TRSM_GRAM_TRAFFIC = 4 * (268658432 + 218687488)
 
 
@@ -347,49 +347,62 @@ def run_ours(args):
         del Q64, ws64
 
     # End to end through the public call, streaming: every step copies its X from pinned host
-    # memory, factors it and copies Q and R back.  Two device buffer sets and three streams let
-    # step s+1's upload and step s-1's download run while step s is factored (the copies of
-    # every timed step are inside the timed region).  Host buffers are flat pinned arrays viewed
-    # column-major, so each transfer is one contiguous copy.
+    # memory, factors it and copies Q and R back.  Three device buffer sets (X, Q, R, rank,
+    # status and workspace each, allocated once, so no buffer changes hands between streams)
+    # on three streams let step s+1's upload, step s's factorization and step s-1's download
+    # run at the same time; every timed step's copies are inside the timed region.  Host
+    # buffers are flat pinned arrays viewed column-major, so each transfer is one copy.
     Xh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
     Xh_flat.view(N, m).t().copy_(X32)
     Qh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
     Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
+    NSETS = 3
     bufs = []
-    for _ in range(2):
+    for _ in range(NSETS):
         Xd = rc.colmajor(m, N, torch.float32, dev)
         Qd = rc.colmajor(m, N, torch.float32, dev)
+        Rd = rc.colmajor(N, N, torch.float64, dev)
+        rkd = torch.empty(1, dtype=torch.int64, device=dev)
+        std = torch.zeros(2, dtype=torch.int32, device=dev)
         wsd = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.DIRECT2, rc.F32) + 256, dtype=torch.uint8,
                           device=dev)
-        bufs.append((Xd, Xd.t().reshape(-1), Qd, Qd.t().reshape(-1), wsd))
+        bufs.append((Xd, Xd.t().reshape(-1), Qd, Qd.t().reshape(-1), Rd, rkd, std, wsd))
     s_in, s_run, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def e2e_steps(count):
-        done_out = [None, None]        # event: buffer set's previous Q download finished
+    def e2e_steps(count, marks=None):
+        done_out = [None] * NSETS       # event: the buffer set's previous Q download finished
         for s in range(count):
-            Xd, Xf, Qd, Qf, wsd = bufs[s % 2]
+            Xd, Xf, Qd, Qf, Rd, rkd, std, wsd = bufs[s % NSETS]
+            ev = {}
             with torch.cuda.stream(s_in):
-                if done_out[s % 2] is not None:
-                    s_in.wait_event(done_out[s % 2])
+                if done_out[s % NSETS] is not None:
+                    s_in.wait_event(done_out[s % NSETS])
+                if marks is not None:
+                    ev["up0"] = torch.cuda.Event(enable_timing=True)
+                    ev["up0"].record(s_in)
                 Xf.copy_(Xh_flat, non_blocking=True)
-                up = torch.cuda.Event()
+                up = torch.cuda.Event(enable_timing=marks is not None)
                 up.record(s_in)
             with torch.cuda.stream(s_run):
                 s_run.wait_event(up)
-                _, Rd_, _, _, _ = rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Qd, workspace=wsd)
-                ran = torch.cuda.Event()
+                rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Qd, workspace=wsd, R=Rd, rank=rkd,
+                               status=std)
+                ran = torch.cuda.Event(enable_timing=marks is not None)
                 ran.record(s_run)
             with torch.cuda.stream(s_out):
                 s_out.wait_event(ran)
                 Qh_flat.copy_(Qf, non_blocking=True)
-                Rh.copy_(Rd_, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s_out)
-                done_out[s % 2] = ev
+                Rh.copy_(Rd, non_blocking=True)
+                dn = torch.cuda.Event(enable_timing=marks is not None)
+                dn.record(s_out)
+                done_out[s % NSETS] = dn
+            if marks is not None:
+                ev.update(up=up, ran=ran, dn=dn)
+                marks.append(ev)
         for st_ in (s_in, s_run, s_out):
             stream.wait_stream(st_)
 
-    e2e_steps(2)
+    e2e_steps(NSETS)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -406,9 +419,39 @@ def run_ours(args):
         t = torch.tensor([ms_e2e], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t[0])
+    # where the streamed steps' time goes (an untimed run with an event at every phase boundary):
+    # per step the upload, factorization and download intervals, and the mean period
+    marks = []
+    e2e_steps(6, marks)
+    torch.cuda.synchronize()
+    t0 = marks[0]["up0"]
+    tl = [{"up": (t0.elapsed_time(mk["up0"]), t0.elapsed_time(mk["up"])),
+           "run": (t0.elapsed_time(mk["up"]), t0.elapsed_time(mk["ran"])),
+           "down": (t0.elapsed_time(mk["ran"]), t0.elapsed_time(mk["dn"]))} for mk in marks]
+    period = (tl[-1]["down"][1] - tl[1]["down"][1]) / (len(tl) - 2)
     Xf0, Qf0 = bufs[0][1], bufs[0][3]
     ms_h2d = timed(lambda: Xf0.copy_(Xh_flat, non_blocking=True), 3, 1)
     ms_d2h = timed(lambda: Qh_flat.copy_(Qf0, non_blocking=True), 3, 1)
+
+    def both():
+        with torch.cuda.stream(s_in):
+            Xf0.copy_(Xh_flat, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            Qh_flat.copy_(bufs[1][3], non_blocking=True)
+        for st_ in (s_in, s_out):
+            stream.wait_stream(st_)
+
+    def both_timed():
+        for st_ in (s_in, s_out):
+            st_.wait_stream(stream)
+        both()
+    ms_both = timed(both_timed, 3, 1)
+    e2e_timeline = {"period_ms": round(period, 3),
+                    "upload_ms": round(statistics.median(b - a for a, b in (t["up"] for t in tl)), 3),
+                    "factor_ms": round(statistics.median(b - a for a, b in (t["run"] for t in tl)), 3),
+                    "download_ms": round(statistics.median(b - a for a, b in (t["down"] for t in tl)), 3),
+                    "h2d_and_d2h_together_ms": round(ms_both, 3),
+                    "steps": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in t.items()} for t in tl]}
 
     variants = None
     if not args.no_variants and m == M:
@@ -465,7 +508,8 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8,
-                    "ms_per_step": round(ms_e2e, 3), "h2d_ms": round(ms_h2d, 3), "d2h_ms": round(ms_d2h, 3)},
+                    "ms_per_step": round(ms_e2e, 3), "h2d_ms": round(ms_h2d, 3), "d2h_ms": round(ms_d2h, 3),
+                    "buffer_sets": NSETS, "timeline": e2e_timeline},
             "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
         }

@@ -66,12 +66,28 @@ typedef enum {
 
 typedef enum { RCQR_F64 = 0, RCQR_F32 = 1, RCQR_BF16 = 2 } rcqr_prec;
 
+/* Diagnostics: the bound of every device-side wait in the tensor-core
+ * sketch's pipeline, in rounds of one mbarrier poll and a sleep of at most
+ * 256 ns, for all later calls of this process; 0 restores the default of 2^22
+ * rounds (about one second).  A wait that runs out stops the kernel from
+ * issuing further tensor-core work; the kernel then waits (always with the
+ * default bound) for the work already issued, writes NaN partial sums and sets
+ * dev_status = {RCQR_ETIMEOUT, -1}.  Returns the previous bound.  Host-side and
+ * not stream-ordered: change it only while no sketch is queued. */
+uint32_t rcqr_set_wait_polls(uint32_t polls);
+
 /* Human-readable name of a status code (static string). */
 const char *rcqr_status_string(int status);
 
-/* Bytes of workspace rcqr_factor / rcqr_reduced / rcqr_sketch need for these
- * sizes (an upper bound valid for all three). 0 on invalid sizes. */
+/* Bytes of workspace rcqr_factor / rcqr_sketch and the other single-problem
+ * calls need for these sizes (an upper bound valid for all of them, and for
+ * rcqr_reduced with L = NULL). 0 on invalid sizes. */
 size_t rcqr_workspace_size(int64_t m, int64_t n, int64_t k, int variant, int prec);
+
+/* Bytes of workspace rcqr_reduced needs: l = the row count of an explicit
+ * extractor L, or 0 for L = Theta (this also counts the l x n buffer of
+ * Y = L X).  0 on invalid sizes. */
+size_t rcqr_reduced_workspace_size(int64_t m, int64_t n, int64_t k, int64_t l, int prec);
 
 /* Host: write the 256 integer levels T[t] of Theta (see above) to out[0..255].
  * Returns RCQR_OK. */
@@ -180,7 +196,11 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
 /* Reduced RCholeskyQR, Alg. 5:  P = Theta X, Y = L X, [S, R] = QR(P),
  * Z = Y R^{-1}.  L: l x m double extractor (ldl >= l), or NULL for L = Theta
  * (then l must equal k and Z = P R^{-1}, the sketch of Q).  Z: l x n,
- * S: k x n (nullable), R: n x n. */
+ * S: k x n (nullable), R: n x n (diag(R) >= 0, the Householder R of P).
+ * S is formed as P R^{-1} by substitution: the orthonormal factor of P up to
+ * rounding amplified by cond(P) (the Householder S and P R^{-1} agree in exact
+ * arithmetic).  Workspace: rcqr_reduced_workspace_size(m, n, k, L ? l : 0,
+ * prec) bytes, checked before anything is queued. */
 rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                          int64_t k, uint64_t seed, const double *L, int64_t l, int64_t ldl,
                          double *Z, int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
@@ -227,8 +247,11 @@ size_t rcqr_batched_workspace_size(const rcqr_problem *probs, int count, int var
  * problems; problem i uses Theta with Philox stream index i.  The problems are
  * spread over library-owned streams forked from `stream` by an event and
  * joined back, so the call can be recorded by a stream capture on `stream`
- * (make the first call on a device before capturing: it creates the streams
- * and loads constants).  Q must not alias X.  Argument errors of any problem
+ * (make the first call on a device before capturing: it creates the streams).
+ * Calls from several host threads on one device take turns (a per-device
+ * lock is held from the fork to the join). Problem i's arguments are read from
+ * the host array when the call is made; the array may be reused once the call
+ * returns (a graph captured from the call keeps the values it saw).  Q must not alias X.  Argument errors of any problem
  * return RCQR_EINVAL before anything is queued. */
 rcqr_status rcqr_factor_batched(const rcqr_problem *probs, int count, int variant, int prec, double tau,
                                 void *workspace, size_t ws_bytes, cudaStream_t stream);

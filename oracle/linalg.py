@@ -128,6 +128,26 @@ def forward_substitution(X, R):
     return Q
 
 
+def forward_substitution_f32(X, R):
+    """forward_substitution in IEEE single precision: X and R rounded to float32 once, then every
+    operation of q_j = (x_j - sum_{i<j} q_i R_ij) / R_jj in float32 (numpy float32 arithmetic).
+
+    This is the bulk step of the multi-precision model of Sec. 1.3 and Sec. 5 with the working
+    precision u = 2^-24 (the paper's float32 experiments, Sec. 6): the dominant operation in u, the
+    sketch and the small factorization (done by the callers) in FP64.
+    """
+    X = np.asarray(X, dtype=np.float32)
+    R = np.asarray(R, dtype=np.float32)
+    m, n = X.shape
+    Q = np.empty((m, n), dtype=np.float32)
+    for j in range(n):
+        acc = X[:, j].copy()
+        for i in range(j):
+            acc -= Q[:, i] * R[i, j]
+        Q[:, j] = acc / R[j, j]
+    return Q
+
+
 def cholesky(A):
     """Upper R with R^T R = A (textbook column Cholesky); NotSPD(j) on a pivot <= 0."""
     A = np.asarray(A, dtype=np.float64)

@@ -69,6 +69,14 @@ def rcholqr(X, k, seed, stream=0):
     return rcholqr_from_sketch(X, P)
 
 
+def rcholqr_f32(X, k, seed, stream=0):
+    """Alg. 2 in the multi-precision form of Sec. 1.3 / Sec. 5: the sketch and the Householder QR
+    in FP64 (u_f), the substitution Q = X R^{-1} in float32 (u = 2^-24).  Returns (Q float32, S, R)."""
+    P = sketch(X, k, seed, stream=stream)
+    S, R = linalg.householder_qr(P)
+    return linalg.forward_substitution_f32(X, R), S, R
+
+
 def cholqr_pass(Q, R):
     """Alg. 3 steps 2-4 applied to (Q, R): returns (Q <- Q R'^{-1}, R <- R' R, R')."""
     A = Q.T @ Q

@@ -30,6 +30,8 @@ _i64, _u64, _i32, _dbl, _vp, _sz = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_in
 _SIGS = {
     "rcqr_status_string": (ctypes.c_char_p, [_i32]),
     "rcqr_workspace_size": (_sz, [_i64, _i64, _i64, _i32, _i32]),
+    "rcqr_reduced_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i32]),
+    "rcqr_set_wait_polls": (ctypes.c_uint32, [ctypes.c_uint32]),
     "rcqr_theta_table": (_i32, [_vp]),
     "rcqr_theta_scale": (_dbl, [_i64]),
     "rcqr_sketch": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
@@ -97,6 +99,15 @@ def status_string(s):
 
 def rcqr_workspace_size(m, n, k, variant=DIRECT, prec=F64):
     return int(lib.rcqr_workspace_size(m, n, k, variant, prec))
+
+
+def rcqr_reduced_workspace_size(m, n, k, l=0, prec=F64):
+    return int(lib.rcqr_reduced_workspace_size(m, n, k, l, prec))
+
+
+def rcqr_set_wait_polls(polls):
+    """Bound of the sketch pipeline's device waits for later calls (0: the default); returns the previous one."""
+    return int(lib.rcqr_set_wait_polls(polls))
 
 
 def rcqr_theta_table():
@@ -198,17 +209,21 @@ def rcqr_chol_update(A, R, rank=None):
     return Rp, status
 
 
-def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None):
-    """Returns (Q, R, perm, rank, status); perm is None for the direct variants."""
+def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=None, rank=None, status=None):
+    """Returns (Q, R, perm, rank, status); perm is None for the direct variants.  Q, R, rank and
+    status may be given (preallocated buffers); the others are allocated on the current stream."""
     m, n = X.shape
     prec = prec_of(X.dtype)
     dev = X.device
     if Q is None:
         Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, dev)
-    R = colmajor(n, n, torch.float64, dev)
+    if R is None:
+        R = colmajor(n, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev) if variant in (RR, RR2) else None
-    rank = torch.empty(1, dtype=torch.int64, device=dev)
-    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    if rank is None:
+        rank = torch.empty(1, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.zeros(2, dtype=torch.int32, device=dev)
     ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, variant, prec), dev)
     wp, wb = _aligned_ptr(ws)
     _check("rcqr_factor", lib.rcqr_factor(_ptr(X), m, n, _ld(X), prec, k, seed, variant, float(tau), _ptr(Q),
@@ -227,7 +242,7 @@ def rcqr_reduced(X, k, seed, L=None, want_S=True):
     S = colmajor(k, n, torch.float64, dev) if want_S else None
     R = colmajor(n, n, torch.float64, dev)
     status = torch.zeros(2, dtype=torch.int32, device=dev)
-    ws = _workspace(rcqr_workspace_size(m, n, k, DIRECT, prec) + (l * n * 8 + 512), dev)
+    ws = _workspace(rcqr_reduced_workspace_size(m, n, k, l if L is not None else 0, prec), dev)
     wp, wb = _aligned_ptr(ws)
     _check("rcqr_reduced", lib.rcqr_reduced(_ptr(X), m, n, _ld(X), prec, k, seed, _ptr(L), l,
                                             _ld(L) if L is not None else 0, _ptr(Z), _ld(Z), _ptr(S),

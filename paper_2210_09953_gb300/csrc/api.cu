@@ -313,6 +313,23 @@ rcqr_status rcqr_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, in
   return cuda_status(launch_qr_adjoint(Q, m, n, ldq, prec, R, ldr, Qbar, ldqb, Rbar, ldrb, Xbar, ldxb, w, stream));
 }
 
+// Workspace of rcqr_reduced: the factor buffers, Y = L X (explicit L only), then the
+// scratch of the sketch / small QR / substitution / dense left product.
+size_t reduced_workspace(int64_t m, int64_t n, int64_t k, int64_t l, int prec) {
+  Workspace w(nullptr, 0);
+  FactorBuffers b;
+  take_factor_buffers(w, n, k, b);
+  if (l > 0) w.take<double>((size_t)l * n);
+  size_t extra = stage_workspace(m, n, k, prec);
+  if (l > 0) extra = std::max(extra, dense_left_workspace(l, m, n));
+  return ((w.used + 255) & ~size_t(255)) + extra + 512;
+}
+
+size_t rcqr_reduced_workspace_size(int64_t m, int64_t n, int64_t k, int64_t l, int prec) {
+  if (!valid_sizes(m, n, k) || !valid_prec(prec) || l < 0 || l > 2048) return 0;
+  return reduced_workspace(m, n, k, l, prec);
+}
+
 rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                          uint64_t seed, const double *L, int64_t l, int64_t ldl, double *Z,
                          int64_t ldz, double *S, int64_t lds, double *R, int64_t ldr,
@@ -323,7 +340,8 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
   if (L == nullptr && l != k) return RCQR_EINVAL;
   if (L != nullptr && (l < 1 || l > 2048 || ldl < l)) return RCQR_EINVAL;
   if (ldz < l) return RCQR_EINVAL;
-  if (!workspace || !aligned(workspace) || ws_bytes < rcqr_workspace_size(m, n, k, 0, prec))
+  // every size check happens here, before anything is queued
+  if (!workspace || !aligned(workspace) || ws_bytes < reduced_workspace(m, n, k, L ? l : 0, prec))
     return RCQR_EWORKSPACE;
   Workspace w(workspace, ws_bytes);
   FactorBuffers b;
@@ -345,15 +363,18 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
   } while (0)
   if (dev_status) RCQR_TRY(launch_reset_status(dev_status, stream));
   // Alg. 5 step 1
-  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, nullptr, *scratch(), stream));
+  RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, 0, 0, b.P, k, nullptr, *scratch(), stream, dev_status));
   if (L) RCQR_TRY(launch_dense_left(L, l, ldl, X, m, n, ldx, prec, Y, l, *scratch(), stream));
-  // Alg. 5 step 2
-  RCQR_TRY(launch_small_qr(b.P, k, n, k, S, lds, R, ldr, *scratch(), stream));
+  // Alg. 5 step 2: R of P = S R (the multi-CTA Householder R); S = P R^{-1}, the
+  // orthonormal sketch of Q = X R^{-1}, by substitution against that R
+  RCQR_TRY(launch_small_r(b.P, k, n, k, R, ldr, *scratch(), stream));
+  if (S) RCQR_TRY(launch_trsm(b.P, k, n, k, RCQR_F64, R, ldr, nullptr, nullptr, S, lds, *scratch(), stream));
   // Alg. 5 step 3: Z = Y R^{-1} (Y = P when L = Theta)
-  RCQR_TRY(launch_trsm(L ? Y : b.P, l, n, l == k && !L ? k : l, RCQR_F64, R, ldr, nullptr, nullptr,
-                       Z, ldz, *scratch(), stream));
+  RCQR_TRY(launch_trsm(L ? Y : b.P, l, n, l, RCQR_F64, R, ldr, nullptr, nullptr, Z, ldz, *scratch(), stream));
 #undef RCQR_TRY
   return RCQR_OK;
 }
+
+uint32_t rcqr_set_wait_polls(uint32_t polls) { return set_wait_polls(polls); }
 
 }  // extern "C"

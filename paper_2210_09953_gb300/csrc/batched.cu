@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
@@ -39,11 +40,47 @@ struct DevStreams {
   cudaStream_t s[kMaxStreams];
   cudaEvent_t fork;
   cudaEvent_t join[kMaxStreams];
+  // held from the fork to the join of one call: concurrent calls on one device
+  // (from several host threads) take turns instead of interleaving their events
+  std::mutex call_mu;
 };
 
 std::mutex g_mu;
 DevStreams g_streams[64];
-int g_best_streams[64] = {0};
+std::atomic<int> g_best_streams[64];
+
+// Fork of the library streams from the caller's stream; the join back runs on
+// every exit path (also after an error), so a stream capture on the caller's
+// stream always ends with every forked branch joined.
+struct ForkGuard {
+  DevStreams *d;
+  cudaStream_t stream;
+  int n = 0;
+  ForkGuard(DevStreams *dd, cudaStream_t st) : d(dd), stream(st) {}
+  bool fork(int ns) {
+    if (cudaEventRecord(d->fork, stream) != cudaSuccess) return false;
+    for (int s2 = 0; s2 < ns; ++s2) {
+      if (cudaStreamWaitEvent(d->s[s2], d->fork, 0) != cudaSuccess) {
+        n = s2;
+        return false;
+      }
+    }
+    n = ns;
+    return true;
+  }
+  bool join() {
+    bool ok = true;
+    for (int s2 = 0; s2 < n; ++s2) {
+      ok = cudaEventRecord(d->join[s2], d->s[s2]) == cudaSuccess && ok;
+      ok = cudaStreamWaitEvent(stream, d->join[s2], 0) == cudaSuccess && ok;
+    }
+    n = 0;
+    return ok;
+  }
+  ~ForkGuard() {
+    if (n) join();
+  }
+};
 
 cudaError_t device_streams(DevStreams **out) {
   int dev = 0;
@@ -67,9 +104,10 @@ cudaError_t device_streams(DevStreams **out) {
 int default_streams(int count) {
   int dev = 0;
   cudaGetDevice(&dev);
-  int ns = (dev >= 0 && dev < 64 && g_best_streams[dev] > 0) ? g_best_streams[dev] : 8;
+  const int tuned = (dev >= 0 && dev < 64) ? g_best_streams[dev].load() : 0;
+  int ns = tuned > 0 ? tuned : 8;
   if (const char *path = std::getenv("RCQR_TUNE_CACHE")) {
-    if (!(dev >= 0 && dev < 64 && g_best_streams[dev] > 0)) {
+    if (tuned <= 0) {
       if (FILE *f = std::fopen(path, "r")) {
         int v = 0;
         if (std::fscanf(f, " { \"batched_streams\" : %d", &v) == 1 && v >= 1 && v <= kMaxStreams) ns = v;
@@ -133,21 +171,9 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
       off += al(qrcp_work_doubles(p.k, p.n) * 8);
     }
   }
-  auto fork = [&](int nstreams) -> bool {
-    if (cudaEventRecord(d->fork, stream) != cudaSuccess) return false;
-    for (int s2 = 0; s2 < nstreams; ++s2)
-      if (cudaStreamWaitEvent(d->s[s2], d->fork, 0) != cudaSuccess) return false;
-    return true;
-  };
-  auto join = [&](int nstreams) -> bool {
-    for (int s2 = 0; s2 < nstreams; ++s2) {
-      if (cudaEventRecord(d->join[s2], d->s[s2]) != cudaSuccess) return false;
-      if (cudaStreamWaitEvent(stream, d->join[s2], 0) != cudaSuccess) return false;
-    }
-    return true;
-  };
+  ForkGuard fg(d, stream);
   // (A) status, column norms and sketch
-  if (!fork(ns)) return RCQR_ECUDA;
+  if (!fg.fork(ns)) return RCQR_ECUDA;
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
     const rcqr_problem &p = probs[i];
@@ -158,11 +184,11 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
                       p.dev_status) != cudaSuccess)
       return RCQR_ECUDA;
   }
-  if (!join(ns)) return RCQR_ECUDA;
+  if (!fg.join()) return RCQR_ECUDA;
   // (B) the QRCPs, one CTA each
   const int nlaunch = (count + kQrcpJobsPerLaunch - 1) / kQrcpJobsPerLaunch;
   const int nb = std::min(nlaunch, kMaxStreams);
-  if (!fork(nb)) return RCQR_ECUDA;
+  if (!fg.fork(nb)) return RCQR_ECUDA;
   std::vector<QrcpJob> jobs(count);
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
@@ -173,11 +199,11 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
     const int b0 = c * kQrcpJobsPerLaunch, cnt = std::min(kQrcpJobsPerLaunch, count - b0);
     if (launch_qrcp_jobs(jobs.data() + b0, cnt, tau, d->s[c % nb]) != cudaSuccess) return RCQR_ECUDA;
   }
-  if (!join(nb)) return RCQR_ECUDA;
+  if (!fg.join()) return RCQR_ECUDA;
   // (C) substitution (Alg. 7 step 4) and, for RR2, one CholeskyQR pass (Alg. 3 steps 2-4)
   const bool pass2 = variant == RCQR_RR2;
   const int qprec = prec == RCQR_F64 ? RCQR_F64 : RCQR_F32;
-  if (!fork(ns)) return RCQR_ECUDA;
+  if (!fg.fork(ns)) return RCQR_ECUDA;
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
     const rcqr_problem &p = probs[i];
@@ -207,7 +233,7 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
         return RCQR_ECUDA;
     }
   }
-  if (!join(ns)) return RCQR_ECUDA;
+  if (!fg.join()) return RCQR_ECUDA;
   return RCQR_OK;
 }
 
@@ -222,11 +248,11 @@ rcqr_status run_batch(const rcqr_problem *probs, int count, int variant, int pre
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return probs[a].m * probs[a].n > probs[b].m * probs[b].n;
   });
+  std::lock_guard<std::mutex> call_lock(d->call_mu);
   if (rank_revealing(variant))
     return run_batch_rr(probs, count, variant, prec, tau, workspace, ws_bytes, stream, ns, d, order);
-  if (cudaEventRecord(d->fork, stream) != cudaSuccess) return RCQR_ECUDA;
-  for (int s = 0; s < ns; ++s)
-    if (cudaStreamWaitEvent(d->s[s], d->fork, 0) != cudaSuccess) return RCQR_ECUDA;
+  ForkGuard fg(d, stream);
+  if (!fg.fork(ns)) return RCQR_ECUDA;
   rcqr_status st = RCQR_OK;
   for (int t = 0; t < count && st == RCQR_OK; ++t) {
     const int i = order[t];
@@ -236,10 +262,7 @@ rcqr_status run_batch(const rcqr_problem *probs, int count, int variant, int pre
     st = factor_impl(p.X, p.m, p.n, p.ldx, prec, p.k, p.seed, (uint32_t)i, variant, tau, p.Q, p.ldq, p.R,
                      p.ldr, p.perm, p.rank, ws, slice, p.dev_status, d->s[s]);
   }
-  for (int s = 0; s < ns; ++s) {
-    if (cudaEventRecord(d->join[s], d->s[s]) != cudaSuccess) return RCQR_ECUDA;
-    if (cudaStreamWaitEvent(stream, d->join[s], 0) != cudaSuccess) return RCQR_ECUDA;
-  }
+  if (!fg.join() && st == RCQR_OK) return RCQR_ECUDA;
   return st;
 }
 
@@ -304,7 +327,7 @@ rcqr_status rcqr_tune_batched(const rcqr_problem *probs, int count, int variant,
   cudaEventDestroy(b);
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64) g_best_streams[dev] = best;
+  if (dev >= 0 && dev < 64) g_best_streams[dev].store(best);
   if (const char *path = std::getenv("RCQR_TUNE_CACHE")) {
     if (FILE *f = std::fopen(path, "w")) {
       std::fprintf(f, "{ \"batched_streams\" : %d, \"ms_per_batch\" : %.4f }\n", best, best_ms / 3.0f);

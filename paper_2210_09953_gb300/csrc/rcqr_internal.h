@@ -38,6 +38,11 @@ struct Workspace {
 
 int num_sms();
 
+// Bound of the device-side pipeline waits of the tensor-core kernels (rounds of
+// one poll and a short sleep); set_wait_polls(0) restores the default (about 1 s).
+uint32_t wait_polls();
+uint32_t set_wait_polls(uint32_t polls);
+
 // Raise a kernel's dynamic shared-memory limit on the current device, once:
 // later calls (for instance inside a stream capture) make no CUDA call.
 cudaError_t ensure_smem(const void *func, int bytes);

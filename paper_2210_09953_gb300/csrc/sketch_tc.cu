@@ -41,6 +41,7 @@
 // Every wait is bounded; a timeout marks the partial sums NaN and raises
 // RCQR_ETIMEOUT in the status word.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "rcqr_internal.h"
@@ -48,8 +49,6 @@
 #include "umma.cuh"
 
 namespace rcqr {
-
-__constant__ int8_t c_theta_levels[256];
 
 namespace {
 
@@ -112,19 +111,23 @@ struct TcArgs {
   double *partial;    // [groups][n][k]
   long long *acc64;   // int64 accumulators, KCH * NC * 128 per CTA
   int *status;        // nullable
+  uint32_t polls;     // bound of every pipeline wait (rounds of poll + sleep)
+  ThetaTable theta;   // the 256 levels T[t], passed by value (no device state to set up)
 };
 
 constexpr int EMPTY_EXP = -0x40000000;
 
-// Exponent of the largest |x| of a block column (from its magnitude bits):
-// EMPTY_EXP for an all-zero (or subnormal-only) column.
+// Exponent floor(log2 |x|) of the largest |x| of a block column, from its
+// magnitude bits (subnormal values included): EMPTY_EXP for an all-zero column.
 __device__ __forceinline__ int block_exp(uint32_t maxbits) {
+  if (maxbits == 0) return EMPTY_EXP;
   const int be = (int)(maxbits >> 23);
-  return be == 0 ? EMPTY_EXP : be - 127;
+  return be != 0 ? be - 127 : (31 - __clz((int)maxbits)) - 149;
 }
 __device__ __forceinline__ int block_exp(unsigned long long maxbits) {
+  if (maxbits == 0) return EMPTY_EXP;
   const int be = (int)((maxbits >> 52) & 0x7FF);
-  return be == 0 ? EMPTY_EXP : be - 1023;
+  return be != 0 ? be - 1023 : (63 - __clzll((long long)maxbits)) - 1074;
 }
 
 __device__ __forceinline__ uint32_t mag_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
@@ -203,9 +206,11 @@ __device__ __forceinline__ void slice8_store(const typename SliceCfg<PREC>::T (&
       const int be = (int)((bits >> 52) & 0x7FF);
       neg |= (uint32_t)(bits >> 63) << t;
       unsigned long long f = 0;
-      if (be != 0 && e != EMPTY_EXP) {
-        const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int d = e - (be - 1023);           // >= 0: x is not larger than the block maximum
+      if ((bits << 1) != 0 && e != EMPTY_EXP) {
+        // |x| = mant 2^(bx - 1075), with bx = 1 and no implicit bit for a subnormal x
+        const unsigned long long frac = bits & 0xFFFFFFFFFFFFFull;
+        const unsigned long long mant = be != 0 ? (frac | (1ull << 52)) : frac;
+        const int d = e - ((be != 0 ? be : 1) - 1023);   // |x| < 2^(e+1): the shift keeps f below 2^56
         f = d <= 3 ? (mant << (3 - d)) : (d - 3 < 64 ? (mant >> (d - 3)) : 0ull);
       }
       F[t] = f;                                  // |x| 2^(55-e), below 2^56
@@ -333,10 +338,11 @@ struct ThetaCalls {
 // Bounded mbarrier wait with growing sleeps between polls (a waiting warp
 // leaves the issue slots to the working ones); gives up at once when another
 // thread of the CTA has already timed out.
-__device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int *fail, uint32_t max_sleep_ns) {
+__device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int *fail, uint32_t max_sleep_ns,
+                                             uint32_t polls) {
   volatile int *f = fail;
   uint32_t ns = 16;
-  for (uint32_t round = 0; round < kWaitPolls; ++round) {
+  for (uint32_t round = 0; round < polls; ++round) {
     if (umma::mbar_wait(bar, parity, 1)) return;
     if (*f) return;
     __nanosleep(ns);
@@ -368,6 +374,7 @@ struct Tc {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
     uint64_t accf;
+    uint64_t drain;      // completion of the MMA thread's last MMAs, before TMEM is released
     uint32_t tslot;
     int s_fail;
     int E_col[2][NC];    // running exponents of the int64 accumulators (by block parity)
@@ -383,7 +390,7 @@ struct Tc {
     const int ft = threadIdx.x - 32 * kFoldWarp0, lane = threadIdx.x & 31, lq = (threadIdx.x >> 5) & 3;
     const int *eb = a.eblk + (blk - a.blk0) * a.n;
     for (int jl = ft; jl < NC; jl += 128) sh.e_blk[jl] = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
-    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256);
+    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256, a.polls);
     umma::fence_after_sync();
     umma::named_sync(128);
     const bool last = b == NB - 1;
@@ -568,7 +575,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   long long *Acc = a.acc64 + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (KCH * NC * 128);
 
   for (int e = tid; e < 256 * 32; e += kThreadsTC) {
-    const int lev = (int)c_theta_levels[e >> 5];
+    const int lev = (int)a.theta.level[e >> 5];
     table[e] = __float_as_uint((float)lev) >> 16;
   }
   for (int j = tid; j < NC; j += kThreadsTC) sh.E_col[0][j] = EMPTY_EXP;
@@ -578,6 +585,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       umma::mbar_init(&sh.empty[s], 1);
     }
     umma::mbar_init(&sh.accf, 1);
+    umma::mbar_init(&sh.drain, 1);
     sh.s_fail = 0;
   }
   if (warp == 0) umma::tmem_alloc(&sh.tslot, K::NCOLS);
@@ -593,7 +601,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     calls.init(tid, kgi);
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
       const int b = it / kSPB, st = it % kSPB;
       calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, (bb + b) * kBlockRows + st * kBK, a);
       umma::fence_proxy_async();
@@ -657,7 +665,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
         for (int u = 0; u < TPT; ++u) e_cur[u] = e_nxt[u];
       }
       cp_async_wait<kXAhead>();
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256);
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
       unsigned char *sB = stage_base + slot * K::STAGE_BYTES + K::A_BYTES;
       const unsigned char *src = xring + (it % kXSlots) * SLOT_BYTES;
 #pragma unroll
@@ -688,8 +696,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       const int b = it / kSPB, st = it % kSPB;
-      if (lane == 0) {
-        wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail, 64);
+      // once any wait of the CTA has given up, no further MMA is issued (the partial sums
+      // become NaN below), so nothing new is in flight when TMEM is released
+      if (lane == 0) wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail, 64, a.polls);
+      if (lane == 0 && *(volatile int *)&sh.s_fail == 0) {
         umma::fence_after_sync();
         const uint32_t a0 = umma::smem_u32(stage_base + slot * K::STAGE_BYTES);
         const uint32_t b0 = a0 + K::A_BYTES;
@@ -719,6 +729,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       __syncwarp();
       if (st == kSPB - 1) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g, bb + b);
     }
+    // drain: the barrier completes once every MMA this thread issued has finished
+    // writing TMEM (at once if none was issued); bounded by the default limit, so a
+    // shortened test limit cannot release TMEM under a running MMA
+    if (lane == 0) {
+      umma::mma_commit(&sh.drain);
+      if (!umma::mbar_wait(&sh.drain, 0u, kWaitPolls)) sh.s_fail = 1;
+    }
+    __syncwarp();
   }
 
   // every thread is done: the last fold consumed the last MMAs and read TMEM
@@ -729,10 +747,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       const int i = kgi * KCH * 128 + il, j = col0 + jl;
       if (i < a.k && j < a.n) a.partial[((int64_t)g * a.n + j) * a.k + i] = __longlong_as_double(0x7FF8000000000000ll);
     }
-    if (tid == 0 && a.status) {
-      a.status[0] = RCQR_ETIMEOUT;
-      a.status[1] = -1;
-    }
+    if (tid == 0 && a.status && atomicCAS(a.status, 0, (int)RCQR_ETIMEOUT) == 0) a.status[1] = -1;
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -813,6 +828,16 @@ cudaError_t launch_tc_prec(const TcArgs &a, const TcPlan &p, dim3 grid, cudaStre
 
 }  // namespace
 
+namespace {
+std::atomic<uint32_t> g_wait_polls{kWaitPolls};
+}  // namespace
+
+uint32_t wait_polls() { return g_wait_polls.load(std::memory_order_relaxed); }
+
+uint32_t set_wait_polls(uint32_t polls) {
+  return g_wait_polls.exchange(polls == 0 ? kWaitPolls : polls, std::memory_order_relaxed);
+}
+
 bool sketch_tc_supported(int64_t n, int64_t k) {
   (void)k;
   return n >= 1 && n <= 256;
@@ -831,14 +856,6 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, 
 cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                              uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                              int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st) {
-  static bool table_ready[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !table_ready[dev]) {
-    cudaError_t e = cudaMemcpyToSymbol(c_theta_levels, theta_table().level, 256);
-    if (e != cudaSuccess) return e;
-    table_ready[dev] = true;
-  }
   const TcPlan p = plan_tc(m, n, k, row_offset, prec);
   double *partial = ws.take<double>((size_t)p.groups * n * k);
   long long *acc64 = ws.take<long long>(acc64_count(p));
@@ -869,6 +886,8 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   a.acc64 = acc64;
   a.eblk = eblk;
   a.status = dev_status;
+  a.polls = wait_polls();
+  a.theta = theta_table();
   dim3 grid((unsigned)(p.kgrp * p.ngrp), (unsigned)p.groups);
   cudaError_t e;
   {

@@ -545,10 +545,8 @@ __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ld
     }
     s_piv = r;
     *rank_out = r;
-    if (r == 0 && dev_status) {
-      dev_status[0] = RCQR_ERANK0;
-      dev_status[1] = -1;
-    }
+    // the first error of a call is kept (an earlier one, e.g. a timed-out sketch, wins)
+    if (r == 0 && dev_status && atomicCAS(dev_status, 0, (int)RCQR_ERANK0) == 0) dev_status[1] = -1;
   }
   __syncthreads();
   const int r = s_piv;
@@ -630,10 +628,8 @@ chol_factor_kernel(const double *__restrict__ A, int n, int64_t lda, const int64
     __syncthreads();
   }
   if (s_fail >= 0) {
-    if (threadIdx.x == 0 && dev_status) {
-      dev_status[0] = RCQR_ENOTSPD;
-      dev_status[1] = s_fail;
-    }
+    // the first error of a call is kept (an earlier one, e.g. a timed-out sketch, wins)
+    if (threadIdx.x == 0 && dev_status && atomicCAS(dev_status, 0, (int)RCQR_ENOTSPD) == 0) dev_status[1] = s_fail;
   }
   if (use_smem)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x)

@@ -90,3 +90,28 @@ def test_invalid_arguments_return_einval_without_device(rc):
     assert L.rcqr_trsm(fake, 100, 300, 100, 0, fake, 300, None, None, fake, 100, None, 0, None) == -1
     assert L.rcqr_gram(fake, 100, 4, 50, 0, None, fake, 4, ws, 1 << 30, None) == -1
     assert L.rcqr_chol_update(None, 4, 4, None, fake, 4, fake, 4, None, None) == -1
+
+
+def test_reduced_workspace_counts_the_extractor(rc):
+    # an explicit L needs room for Y = L X (l x n doubles) on top of the L = Theta case
+    base = rc.rcqr_reduced_workspace_size(1 << 20, 64, 256, 0, 1)
+    with_l = rc.rcqr_reduced_workspace_size(1 << 20, 64, 256, 2000, 1)
+    assert base > 0 and with_l >= base + 2000 * 64 * 8
+    assert rc.rcqr_reduced_workspace_size(1 << 20, 64, 256, 4000, 1) == 0     # l > 2048
+    # the size check comes first: too small a workspace is refused before anything is queued
+    fake = ctypes.c_void_p(0x1000)
+    L = rc.lib
+    small = rc.rcqr_reduced_workspace_size(100, 4, 16, 0, 0)
+    assert rc.rcqr_reduced_workspace_size(100, 4, 16, 2000, 0) > small
+    assert L.rcqr_reduced(fake, 100, 4, 100, 0, 16, 1, fake, 2000, 2000, fake, 2000, None, 0, fake, 4,
+                          ctypes.c_void_p(0x100000), small, None, None) == -6
+
+
+def test_wait_poll_bound_round_trip(rc):
+    prev = rc.rcqr_set_wait_polls(7)
+    try:
+        assert prev == 1 << 22
+        assert rc.rcqr_set_wait_polls(0) == 7        # 0 restores the default
+        assert rc.rcqr_set_wait_polls(0) == 1 << 22
+    finally:
+        rc.rcqr_set_wait_polls(0)

@@ -122,3 +122,22 @@ def test_triangular_inverse_tiny_bruteforce():
     for vals in itertools.product([1.0, -2.0], [0.5, 3.0], [4.0]):
         R = np.array([[vals[0], 1.0, 2.0], [0.0, vals[1], -1.0], [0.0, 0.0, vals[2]]])
         assert np.allclose(linalg.triangular_inverse(R) @ R, np.eye(3), atol=1e-15)
+
+
+def test_forward_substitution_f32_backward_error_and_exact_case():
+    # Higham Thm 8.5 for the float32 substitution: |X - Q R| <= (n + 2) u32 |Q||R| entrywise (X, R
+    # rounded to float32 first); a dropped term, a transposed R or a wrong index breaks it at once
+    rng = np.random.default_rng(4)
+    m, n = 300, 24
+    R = np.triu(rng.standard_normal((n, n))) + 4 * np.eye(n)
+    X = rng.standard_normal((m, n))
+    Q = linalg.forward_substitution_f32(X, R).astype(np.float64)
+    X32, R32 = X.astype(np.float32).astype(np.float64), R.astype(np.float32).astype(np.float64)
+    u32 = 2.0 ** -24
+    assert np.all(np.abs(X32 - Q @ R32) <= (n + 2) * u32 * (np.abs(Q) @ np.abs(R32)) + 1e-30)
+    bad = linalg.forward_substitution_f32(X, R.T.copy()).astype(np.float64)   # transposed operand
+    assert not np.all(np.abs(X32 - bad @ R32) <= (n + 2) * u32 * (np.abs(bad) @ np.abs(R32)))
+    # small integers, unit upper triangular integer R: every float32 operation is exact
+    Ri = np.triu(rng.integers(-3, 4, (8, 8)).astype(np.float64), 1) + np.eye(8)
+    Qi = rng.integers(-5, 6, (50, 8)).astype(np.float64)
+    assert np.array_equal(linalg.forward_substitution_f32(Qi @ Ri, Ri).astype(np.float64), Qi)

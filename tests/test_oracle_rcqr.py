@@ -190,3 +190,35 @@ def test_cholqr_pass_reports_indefinite_gram():
     with pytest.raises(linalg.NotSPD) as e:
         rcqr.cholqr_pass(Q, np.eye(2))
     assert e.value.j == 1
+
+
+@pytest.mark.parametrize("row_offset", [0, 5, 17, 12345])
+def test_sketch_rows_selects_rows_of_the_sketch(row_offset):
+    """sketch_rows (the checker of the full-size GPU tests) equals the selected rows of sketch,
+    bit for bit on integer X (every partial sum exact), for offsets that are not multiples of the
+    16-row Philox counter block and for row blocks that split X unevenly."""
+    rng = np.random.default_rng(row_offset + 3)
+    m, n, k = 1000, 5, 40
+    X = rng.integers(-128, 128, (m, n)).astype(np.float64)
+    rows = np.array([39, 0, 17, 8, 9, 38])
+    full = rcqr.sketch(X, k, 0xC0FFEE, row_offset=row_offset, row_block=333)
+    sel = rcqr.sketch_rows(X, k, 0xC0FFEE, rows, row_offset=row_offset, row_block=157)
+    assert np.array_equal(sel, full[rows])
+    # and a wrong offset is caught (Theta's columns are tied to the global row index)
+    off_by_one = rcqr.sketch_rows(X, k, 0xC0FFEE, rows, row_offset=row_offset + 1, row_block=157)
+    assert not np.array_equal(off_by_one, full[rows])
+
+
+def test_rcholqr_f32_well_conditioned_q():
+    """Alg. 2 with a float32 substitution: Q has the backward error of the float32 substitution and
+    stays well conditioned while u32 * cond stays small (Thm. 5.2 with u = 2^-24)."""
+    m, n, k, kappa = 4000, 16, 256, 1e3        # k = 16 n: eps < 1, both sides of (main2) finite
+    X, U = svd_matrix(m, n, kappa, 9)
+    Q, S, R = rcqr.rcholqr_f32(X, k, 21)
+    Th = theta.theta(21, k, 0, m)
+    eps = rcqr.embedding_epsilon(Th, U)
+    s = np.linalg.svd(Q.astype(np.float64), compute_uv=False)
+    slack = 4 * 2.0 ** -24 * n ** 1.5 * kappa
+    assert eps < 1
+    assert (1 + eps) ** -0.5 - slack <= s.min() and s.max() <= (1 - eps) ** -0.5 + slack
+    assert np.linalg.norm(S - Th @ Q.astype(np.float64)) <= 6.1 * 2.0 ** -24 * n ** 1.5 * kappa

@@ -4,7 +4,7 @@ Some callers (a plugin with a fixed argument list, code inside an application
 that owns all device memory through its own pool) cannot hand the library a
 workspace.  This entry point keeps its partial sums in the library's own
 fixed device array instead.  The test calls it through the C ABI twice in a
-row, on two different shapes, and checks each result against rcqr_sketch
+row, on three different shapes (FP32, FP64 and BF16 X), and checks each result against rcqr_sketch
 (the column-wise tolerance the sketch parity tests state for each precision) and that the calls
 after the first change no device memory usage.  This file is collected last
 so that a failure here does not hide the other tests' results.
@@ -16,8 +16,8 @@ import pytest
 import torch
 
 pytestmark = pytest.mark.gpu
-# the column-wise sketch tolerances the parity tests state (FP64 X / FP32 X)
-SKETCH_TOL = {"f64": 1e-12, "f32": 1e-11}
+# the column-wise sketch tolerances the parity tests state (FP64 X / FP32 X / BF16 X)
+SKETCH_TOL = {"f64": 1e-12, "f32": 1e-11, "bf16": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +53,7 @@ def _colrel(A, B):
 
 def test_noalloc_sketch_matches_workspace_sketch_twice(rc):
     from paper_2210_09953_gb300 import inputs
-    cases = [(20011, 64, 256, "f32", 3), (5003, 7, 64, "f64", 0)]
+    cases = [(20011, 64, 256, "f32", 3), (5003, 7, 64, "f64", 0), (12007, 33, 136, "bf16", 21)]
     _noalloc(rc, inputs.svd_matrix(1000, 4, 10.0, 1, dtype="f64", device="cuda"), 16, 1)   # first call: set-up
     torch.cuda.synchronize()
     free_before = torch.cuda.mem_get_info()[0]
