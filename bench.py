@@ -35,13 +35,11 @@ def workload_name(m):
 
 SEED_X, SEED_THETA = 1002, 0x5EED0002
 ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (about 10-20 s on 16 cores)
-# DRAM bytes (read + write) of the three kernels of one rcqr_sketch call on the 4M x 64 FP32
-# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1M-row launch of each kernel,
-# scaled by 4 (per-row traffic is the same).
-SKETCH_CALL_TRAFFIC = 4 * (268455680 + 140288 + 287843584 + 25611264 + 19934208)
-# the same for trsm32_gram_kernel (X read once, Q written once; the writes still in L2 when
-# the kernel ends are not counted)
-TRSM_GRAM_TRAFFIC = 4 * (268658432 + 218687488)
+# DRAM bytes (read + write) per call on the 4M x 64 FP32 workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of every kernel of the call, captured on a
+# 1M-row launch and scaled by 4: per-row traffic is the same).  None where the kernels
+# changed after the last capture.
+TRAFFIC = {"sketch": None, "trsm": None, "trsm_gram": None}
 
 
 def parse():
@@ -406,7 +404,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_e2e = max(3, min(args.steps, 10))
+    n_e2e = max(16, args.steps)
     e0.record(stream)
     for st_ in (s_in, s_run, s_out):
         st_.wait_stream(stream)
@@ -464,15 +462,25 @@ def run_ours(args):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    sketch_bytes = m * N * 4                 # algorithmic: X read once
-    achieved = sketch_bytes / (ms_sketch * 1e-3) / 1e9
-    # fused substitution + Gram: algorithmic flops per row = 2 (n(n-1)/2 substitution FMAs
-    # + n(n+1)/2 Gram FMAs); FP32 SIMT peak = SMs x 128 FP32 lanes x 2 flops x max SM clock
-    tg_flops = 2.0 * m * (N * (N - 1) // 2 + N * (N + 1) // 2)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = clocks.get("sm_max_mhz") or 2070
-    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
-    tg_achieved = tg_flops / (ms_tg * 1e-3) / 1e12
+    # rooflines of the three bulk calls of the step, each against the measured HBM bandwidth:
+    # algorithmic bytes = X read once (sketch), X read + Q written (substitution fused with the
+    # Gram, and the in-place pass-2 substitution timed here as X -> Q); `roofline` is the call
+    # with the largest share of the step
+    def roof(name, kernel, nbytes, ms):
+        ach = nbytes / (ms * 1e-3) / 1e9
+        tr = TRAFFIC.get(name) if m == M else None
+        return {"kernel": kernel, "bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": tr, "peak_source": peak_src,
+                "algorithmic_bytes": nbytes, "ms": round(ms, 4)}
+    roofs = {
+        "sketch": roof("sketch", "rcqr_sketch: block_exp_kernel + sketch_tc_kernel + reduction (FP32 X)",
+                       m * N * 4, ms_sketch),
+        "trsm_gram": roof("trsm_gram", "rcqr_trsm_gram: trsm_tc_kernel<GRAM> (blocked substitution on tcgen05 "
+                          "fused with A = Q^T Q) + prep + Gram reduction (FP32 X)", m * N * 8, ms_tg),
+        "trsm": roof("trsm", "rcqr_trsm: trsm_tc_kernel (blocked substitution on tcgen05) + prep (FP32 X -> Q)",
+                     m * N * 8, ms_trsm),
+    }
+    dominant = max(roofs, key=lambda k_: roofs[k_]["ms"])
     # per factorization (mixed path, Alg. 3): status reset, sketch (block exponents, tensor-core
     # sketch, reduction), Householder R + sign fix, rank, substitution prep + substitution fused
     # with the Gram + Gram reduction, Cholesky update, substitution prep + substitution
@@ -495,16 +503,8 @@ def run_ours(args):
             "fp64_path": fp64,
             "variants": variants,
             "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4), "trsm_gram": round(ms_tg, 4)},
-            "roofline": {"kernel": "trsm32_gram_kernel: Q = X R^-1 fused with A = Q^T Q (rcqr_trsm_gram, FP32 X)",
-                         "bound": "alu", "achieved": round(tg_achieved, 3), "peak": round(alu_peak, 2),
-                         "unit": "TFLOP/s", "frac": round(tg_achieved / alu_peak, 4),
-                         "traffic": TRSM_GRAM_TRAFFIC if m == M else None,
-                         "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"},
-            "roofline_sketch": {"kernel": "rcqr_sketch: block_exp_kernel + sketch_tc_kernel + reduction (FP32 X)",
-                                "bound": "hbm", "achieved": round(achieved, 2),
-                                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                                "traffic": SKETCH_CALL_TRAFFIC if m == M else None,
-                                "peak_source": peak_src},
+            "roofline": roofs[dominant],
+            "rooflines": roofs,
             "clocks": clocks,
             "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8,

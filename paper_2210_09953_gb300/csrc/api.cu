@@ -280,7 +280,7 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   if (fused) {
     // the substitution and the Gram of Alg. 3 step 2 in one pass over X
     RCQR_TRY(launch_trsm32_gram(X, m, n, ldx, prec, R, ldr, pm, rkp, (float *)Q, ldq, b.A, n, *scratch(),
-                                stream));
+                                stream, dev_status));
   } else {
     RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream, dev_status));
   }

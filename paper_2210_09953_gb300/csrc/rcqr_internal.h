@@ -139,7 +139,7 @@ bool trsm32_supported(int64_t n);
 size_t trsm32_workspace(int64_t n);
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st);
+                          Workspace &ws, cudaStream_t st, int *dev_status = nullptr);
 int gram32_groups(int64_t m, int64_t n);
 cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
                           double *partial, int groups, cudaStream_t st);
@@ -149,7 +149,15 @@ bool trsm32_gram_supported(int64_t n);
 size_t trsm32_gram_workspace(int64_t m, int64_t n);
 cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                                int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
-                               double *A, int64_t lda, Workspace &ws, cudaStream_t st);
+                               double *A, int64_t lda, Workspace &ws, cudaStream_t st, int *dev_status = nullptr);
+// Blocked substitution on the tensor cores (trsm_tc.cu), 32 < n <= 64: Rf is the 64 x 64
+// FP32 R of trsm32_prep_kernel; with `partial` (trsm_tc_gram_groups(m) n x n FP64
+// blocks) it also writes the per-CTA partial Gram matrices of Q.
+bool trsm_tc_supported(int64_t n);
+int trsm_tc_gram_groups(int64_t m);
+cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
+                           const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                           double *partial, int *status, cudaStream_t st);
 // A = sum of `groups` n x n partials (fixed order), trsm_simt.cu.
 cudaError_t launch_gram_reduce(const double *partial, int groups, int64_t n, double *A, int64_t lda,
                                cudaStream_t st);

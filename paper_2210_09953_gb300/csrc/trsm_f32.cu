@@ -535,7 +535,10 @@ bool trsm32_supported(int64_t n) { return n >= 1 && n <= 256; }
 
 // R in FP32 for the substitution kernels: NB x NB, NB = n rounded up to 16 (row
 // kernel) or to 64 (panel kernel, n > 64).
-int trsm32_nb(int64_t n) { return n > 64 ? (int)((n + 63) / 64) * 64 : (int)((n + 15) / 16) * 16; }
+int trsm32_nb(int64_t n) {
+  if (trsm_tc_supported(n)) return 64;      // the tensor-core kernel's padded width
+  return n > 64 ? (int)((n + 63) / 64) * 64 : (int)((n + 15) / 16) * 16;
+}
 
 size_t trsm32_workspace(int64_t n) {
   const int NB = trsm32_nb(n);
@@ -547,12 +550,14 @@ size_t trsm32_workspace(int64_t n) {
 
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st) {
+                          Workspace &ws, cudaStream_t st, int *dev_status) {
   const int NB = trsm32_nb(n);
   float *Rf = ws.take<float>((size_t)NB * NB);
   float *dinv = ws.take<float>((size_t)NB);
   if (!Rf || !dinv) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
+  if (trsm_tc_supported(n))
+    return launch_trsm_tc(X, m, n, ldx, prec, Rf, dinv, perm, rank, (float *)Q, ldq, nullptr, dev_status, st);
   if (n > 64) {
     const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);
     if (prec == RCQR_BF16)
@@ -580,20 +585,27 @@ size_t trsm32_gram_workspace(int64_t m, int64_t n) {
   Workspace w(nullptr, 0);
   w.take<float>((size_t)64 * 64);
   w.take<float>((size_t)64);
-  w.take<double>((size_t)trsm32_gram_groups(m) * n * n);
+  const int G = trsm_tc_supported(n) ? trsm_tc_gram_groups(m) : trsm32_gram_groups(m);
+  w.take<double>((size_t)G * n * n);
   return w.used;
 }
 
 cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                                int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
-                               double *A, int64_t lda, Workspace &ws, cudaStream_t st) {
-  const int NB = (int)((n + 15) / 16) * 16;
+                               double *A, int64_t lda, Workspace &ws, cudaStream_t st, int *dev_status) {
+  const bool tc = trsm_tc_supported(n);
+  const int NB = tc ? 64 : (int)((n + 15) / 16) * 16;
   float *Rf = ws.take<float>((size_t)64 * 64);
   float *dinv = ws.take<float>((size_t)64);
-  const int G = trsm32_gram_groups(m);
+  const int G = tc ? trsm_tc_gram_groups(m) : trsm32_gram_groups(m);
   double *partial = ws.take<double>((size_t)G * n * n);
   if (!Rf || !dinv || !partial) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
+  if (tc) {
+    cudaError_t e = launch_trsm_tc(X, m, n, ldx, prec, Rf, dinv, perm, rank, Q, ldq, partial, dev_status, st);
+    if (e != cudaSuccess) return e;
+    return launch_gram_reduce(partial, G, n, A, lda, st);
+  }
   const size_t smem = ((size_t)NB * NB + 64 + (size_t)64 * kTGStride) * sizeof(float);
   cudaError_t e = cudaSuccess;
 #define RCQR_TG(NBV)                                                                                     \

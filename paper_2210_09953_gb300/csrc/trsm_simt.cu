@@ -137,9 +137,8 @@ size_t trsm_workspace(int64_t m, int64_t n, int prec) {
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
                         void *Q, int64_t ldq, Workspace &ws, cudaStream_t st, int *dev_status) {
-  (void)dev_status;
   if (prec != RCQR_F64 && trsm32_supported(n))
-    return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st);
+    return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st, dev_status);
   if (prec != RCQR_F64) return cudaErrorInvalidValue;   // n <= 256 always takes the FP32 kernels
   const unsigned blocks = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
   trsm_rows_kernel<double, double><<<blocks, kTrsmThreads, 0, st>>>((const double *)X, m, (int)n, ldx, R, ldr,

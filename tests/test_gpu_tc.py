@@ -1,0 +1,117 @@
+"""GPU parity of the tensor-core blocked substitution (32 < n <= 64, FP32 / BF16 X) and of the
+Gram matrix fused into it, against the oracle.
+
+Tolerances (u = 2^-24, the mixed path's working precision):
+* Q = X R^{-1}: the row-wise backward error of an FP32 substitution, |X - Q R| <=
+  2 (n + 3) u |Q||R| entrywise (Higham Thm. 8.5; the off-diagonal blocks' products are
+  exact three-piece bf16 splits summed in FP32, so they keep that bound), and the forward
+  error against the FP64 oracle substitution, column-wise <= 2 (n + 3) u cond(R) + 2 u.
+* A = Q^T Q from the fused pass: |A - Q^T Q| <= 66 u (|Q|^T |Q|) entrywise, Q^T Q in FP64
+  from the returned Q (the bound the compensated FP32 Gram states).
+Shapes: a single partial tile (m < 128), exact multiples of the 128-row tile, ragged tails,
+n = 33 (one used column in the last 16-column block), n = 48, 64, a permuted rank-deficient
+call (the rank-revealing form of Alg. 7 step 4) and Q in place of X (Alg. 3 step 4).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import linalg as olin
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_09953_gb300 import _binding
+    return _binding
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    from paper_2210_09953_gb300 import inputs as inp
+    return inp
+
+
+def host64(t):
+    return t.detach().to("cpu", torch.float64).numpy()
+
+
+def colrel(A, B):
+    den = np.linalg.norm(B, axis=0)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.linalg.norm(A - B, axis=0) / den))
+
+
+def upper_r(n, cond, seed):
+    from paper_2210_09953_gb300 import inputs as inp
+    Rm = inp.svd_matrix(4 * n, n, cond, seed, dtype="f64", device="cpu").numpy()
+    _, Ro = olin.householder_qr(Rm)
+    return Ro
+
+
+def check_substitution(Xh, Qg, Ro, n, cond):
+    E = np.abs(Xh - Qg @ Ro)
+    assert np.all(E <= 2 * (n + 3) * U32 * (np.abs(Qg) @ np.abs(Ro)) + 1e-300)
+    Qo = olin.forward_substitution(Xh, Ro)
+    assert colrel(Qg, Qo) <= 2 * (n + 3) * U32 * cond + 2 * U32
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n,cond", [(77, 40, 1e3), (128, 64, 1e2), (5000, 33, 1e4), (70001, 64, 1e6),
+                                      (32768, 48, 1e8), (100003, 57, 1e2)])
+def test_tc_substitution_and_fused_gram(rc, inputs, prec, m, n, cond):
+    X = inputs.svd_matrix(m, n, cond, 500 + n, dtype=prec, device=DEV)
+    Ro = upper_r(n, cond, 90 + n)
+    R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
+    Q = rc.rcqr_trsm(X, R)
+    Qf, A = rc.rcqr_trsm_gram(X, R)
+    torch.cuda.synchronize()
+    assert torch.equal(Q, Qf)                         # one substitution arithmetic for both calls
+    Xh, Qg = host64(X), host64(Q)
+    check_substitution(Xh, Qg, Ro, n, cond)
+    Ao = Qg.T @ Qg
+    scale = np.abs(Qg).T @ np.abs(Qg)
+    assert np.all(np.abs(host64(A) - Ao) <= 66 * U32 * scale)
+    assert np.array_equal(host64(A), host64(A).T)
+
+
+def test_tc_substitution_permuted_rank(rc, inputs):
+    m, n, r = 20000, 64, 37
+    X = inputs.svd_matrix(m, n, 1e2, 6, dtype="f32", device=DEV)
+    perm_h = np.random.default_rng(1).permutation(n).astype(np.int32)
+    perm = torch.from_numpy(perm_h).to(DEV)
+    rank = torch.tensor([r], dtype=torch.int64, device=DEV)
+    Ro = np.triu(np.random.default_rng(0).standard_normal((n, n))) + 8 * np.eye(n)
+    R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
+    Q = host64(rc.rcqr_trsm(X, R, perm=perm, rank=rank))
+    Qf, A = rc.rcqr_trsm_gram(X, R, perm=perm, rank=rank)
+    torch.cuda.synchronize()
+    assert np.array_equal(Q, host64(Qf))
+    Xs = host64(X)[:, perm_h[:r]]
+    R11 = Ro[:r, :r].astype(np.float32).astype(np.float64)
+    check_substitution(Xs, Q[:, :r], R11, r, np.linalg.cond(R11))
+    assert np.all(Q[:, r:] == 0)
+    Ag = host64(A)
+    assert np.all(Ag[r:, :] == 0) and np.all(Ag[:, r:] == 0)
+
+
+def test_tc_substitution_in_place(rc, inputs):
+    # Alg. 3 step 4: Q <- Q R'^{-1} with Q overwritten row by row
+    m, n = 50001, 64
+    X = inputs.svd_matrix(m, n, 1e3, 12, dtype="f32", device=DEV)
+    Ro = upper_r(n, 10.0, 13)
+    R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
+    Xh = host64(X)
+    Qs = host64(rc.rcqr_trsm(X.clone(), R))
+    Y = X.clone()
+    rc.rcqr_trsm(Y, R, Q=Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(host64(Y), Qs)
+    check_substitution(Xh, Qs, Ro, n, 10.0)
