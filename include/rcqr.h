@@ -60,8 +60,12 @@ typedef enum {
 typedef enum {
   RCQR_DIRECT = 0,   /* RCholeskyQR, Alg. 2: Q well conditioned */
   RCQR_DIRECT2 = 1,  /* RCholeskyQR2, Alg. 3: Q orthonormal */
-  RCQR_RR = 2,       /* RRRCholQR, Alg. 7 with the column normalisation of Sec. 4 */
-  RCQR_RR2 = 3       /* RRRCholQR followed by one CholeskyQR pass (Sec. 4) */
+  RCQR_RR = 2,       /* RRRCholQR, Alg. 7 with the column normalisation of Sec. 4;
+                        RRQR of step 2 = column-pivoted Householder QR */
+  RCQR_RR2 = 3,      /* RRRCholQR followed by one CholeskyQR pass (Sec. 4) */
+  RCQR_SRR = 4,      /* RRRCholQR whose RRQR is the strong rank-revealing QR of Gu and
+                        Eisenstat with f = 1.5 (Sec. 4, Sec. 6.1; see rcqr_srrqr) */
+  RCQR_SRR2 = 5      /* RCQR_SRR followed by one CholeskyQR pass */
 } rcqr_variant;
 
 typedef enum { RCQR_F64 = 0, RCQR_F32 = 1, RCQR_BF16 = 2 } rcqr_prec;
@@ -143,6 +147,23 @@ rcqr_status rcqr_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp,
                       const double *colnorm2, double tau,
                       double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                       void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
+/* Strong rank-revealing QR for Alg. 7 steps 2-3 (the RRQR of Sec. 4 as Sec. 6.1 runs
+ * it: Gu and Eisenstat's strong RRQR with parameter f, here after column pivoting).
+ * Starts as rcqr_qrcp (same arguments and outputs), then, at the truncation rank r
+ * (0 < r < n), swaps columns while some
+ *   rho_ij = (R11^{-1} R12)_ij^2 + (gamma_j(R22) / omega_i(R11))^2 > f^2
+ * (gamma_j = ||R22[:, j]||_2, omega_i = 1 / ||row i of R11^{-1}||_2; the largest rho_ij,
+ * first in column-major order on ties), trading column i of the leading block with column
+ * r + j and factoring P[:, perm] D^{-1} again (no pivoting).  Each swap multiplies
+ * |det R11| by more than f; at most 4 n swaps per rank, and the rank test is repeated on
+ * the swapped factor (at most 4 rounds while it changes).  On return every rho_ij <= f^2,
+ * which gives sigma_i(R11) >= sigma_i(P D^{-1}) / q and sigma_j(R22) <= sigma_{r+j} q with
+ * q = sqrt(1 + f^2 r (n - r)) (Gu and Eisenstat 1996, Thm. 3.2) -- the RRQR properties
+ * the analysis of Sec. 5.3 assumes.  f >= 1; the variants RCQR_SRR/SRR2 use f = 1.5. */
+rcqr_status rcqr_srrqr(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
+                       double tau, double f, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                       void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
 /* Forward substitution, Alg. 2 step 3:  Q = X R^{-1} (m x n; Q's type follows
  * prec: double for F64, float otherwise).  R is n x n upper with nonzero

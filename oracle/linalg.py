@@ -101,6 +101,75 @@ def qrcp(P):
     return S * sgn[None, :], R * sgn[:, None], perm
 
 
+def back_substitution_upper(U, B):
+    """X with U X = B for upper triangular U (one row of X at a time, from the last)."""
+    U = np.asarray(U, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    r = U.shape[0]
+    X = np.zeros_like(B)
+    for i in reversed(range(r)):
+        X[i] = (B[i] - U[i, i + 1:] @ X[i + 1:]) / U[i, i]
+    return X
+
+
+def swap_ratios(R, r):
+    """rho_ij of Gu & Eisenstat (1996) for the split of R at rank r: with R11 = R[:r, :r],
+    R12 = R[:r, r:], R22 = R[r:, r:],
+        rho_ij = (R11^{-1} R12)_ij^2 + (gamma_j(R22) / omega_i(R11))^2,
+    gamma_j = the 2-norm of column j of R22, omega_i = 1 / (2-norm of row i of R11^{-1}).
+    sqrt(rho_ij) is the factor by which |det R11| grows when column i and column r + j trade
+    places (their Lemma 3.1)."""
+    R11, R12, R22 = R[:r, :r], R[:r, r:], R[r:, r:]
+    W = back_substitution_upper(R11, R12)
+    Rinv = back_substitution_upper(R11, np.eye(r))
+    inv_omega2 = np.sum(Rinv * Rinv, axis=1)
+    gamma2 = np.sum(R22 * R22, axis=0)
+    return W * W + inv_omega2[:, None] * gamma2[None, :]
+
+
+def strong_rrqr_swaps(P, perm, r, f, max_swaps=None):
+    """The swaps of strong RRQR (Gu & Eisenstat 1996, Algorithm 4) at a fixed rank r, from the
+    column order perm: while some rho_ij > f^2, trade column i of the leading block with
+    column r + j (the largest rho_ij, the first one in column-major order on ties) and
+    re-factor P[:, perm] by Householder QR.  Each swap multiplies |det R11| by more than f,
+    so it ends; max_swaps (default 4 n) bounds it in floating point.
+    Returns (S, R, perm, swaps) with P[:, perm] = S R, diag(R) >= 0."""
+    P = np.asarray(P, dtype=np.float64)
+    n = P.shape[1]
+    perm = np.array(perm, copy=True)
+    S, R = householder_qr(P[:, perm])
+    if r <= 0 or r >= n:
+        return S, R, perm, 0
+    limit = 4 * n if max_swaps is None else max_swaps
+    swaps = 0
+    while swaps < limit:
+        rho = swap_ratios(R, r)
+        flat = rho.ravel(order="F")
+        t = int(np.argmax(flat))
+        if not flat[t] > f * f:
+            break
+        i, j = t % r, t // r
+        perm[[i, r + j]] = perm[[r + j, i]]
+        S, R = householder_qr(P[:, perm])
+        swaps += 1
+    return S, R, perm, swaps
+
+
+def strong_rrqr(P, tau, f, rounds=4):
+    """Rank-revealing QR for Alg. 7 steps 2-3 with Gu-Eisenstat swaps: QRCP's order, the
+    truncation rank r (truncation_rank), strong-RRQR swaps at r, and again while the rank
+    of the swapped factor differs (at most `rounds` times).  Returns (S, R, perm, r)."""
+    S, R, perm = qrcp(P)
+    r = truncation_rank(R, tau)
+    for _ in range(rounds):
+        S, R, perm, _ = strong_rrqr_swaps(P, perm, r, f)
+        r_new = truncation_rank(R, tau)
+        if r_new == r:
+            break
+        r = r_new
+    return S, R, perm, r
+
+
 def spectral_norm(A):
     """||A||_2 (largest singular value; numpy's SVD as a library primitive)."""
     if A.size == 0:

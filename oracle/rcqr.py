@@ -101,26 +101,31 @@ def reduced(X, k, seed, L=None):
     return Z, S, R
 
 
-def rrrcholqr(X, k, seed, tau, stream=0):
+def rrrcholqr(X, k, seed, tau, stream=0, strong_f=None):
     """Alg. 7 with column normalisation: returns (Q m x r, S k x r, R r x n, perm, r).
 
-    X[:, perm] ~ Q R.  Zero columns of X are left unscaled (D_j = 1 for them).
+    X[:, perm] ~ Q R.  Zero columns of X are left unscaled (D_j = 1 for them).  The RRQR
+    of step 2 is column-pivoted Householder QR, followed (strong_f = f) by the strong-RRQR
+    swaps of Gu & Eisenstat with parameter f (Sec. 4 and Sec. 6.1 take f = 1.5).
     """
     X = np.asarray(X, dtype=np.float64)
     D = column_norms(X)
     Dsafe = np.where(D > 0, D, 1.0)
     P = sketch(X, k, seed, stream=stream) / Dsafe[None, :]   # P <- P D^{-1}
-    S, R, perm = linalg.qrcp(P)                               # step 2
-    r = linalg.truncation_rank(R, tau)                        # step 3
+    if strong_f is None:
+        S, R, perm = linalg.qrcp(P)                           # step 2
+        r = linalg.truncation_rank(R, tau)                    # step 3
+    else:
+        S, R, perm, r = linalg.strong_rrqr(P, tau, strong_f)  # steps 2-3
     Xsel = X[:, perm[:r]] / Dsafe[perm[:r]][None, :]          # X Pi_{:,1:r} D_sel^{-1}
     Q = linalg.forward_substitution(Xsel, R[:r, :r])          # step 4
     Rout = R[:r, :] * Dsafe[perm][None, :]                    # step 5 and R <- R Pi^T D Pi
     return Q, S[:, :r], Rout, perm, r
 
 
-def rrrcholqr2(X, k, seed, tau, stream=0):
+def rrrcholqr2(X, k, seed, tau, stream=0, strong_f=None):
     """Alg. 7 followed by one CholeskyQR pass: returns (Q, R, perm, r)."""
-    Q, _, R, perm, r = rrrcholqr(X, k, seed, tau, stream)
+    Q, _, R, perm, r = rrrcholqr(X, k, seed, tau, stream, strong_f)
     if r == 0:
         return Q, R, perm, r
     Q2, R2, _ = cholqr_pass(Q, R)

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librcqr.so")
 
 F64, F32, BF16 = 0, 1, 2
-DIRECT, DIRECT2, RR, RR2 = 0, 1, 2, 3
+DIRECT, DIRECT2, RR, RR2, SRR, SRR2 = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "RCQR_OK", -1: "RCQR_EINVAL", -2: "RCQR_ENOTSPD", -3: "RCQR_ERANK0",
                 -4: "RCQR_ECUDA", -5: "RCQR_ETIMEOUT", -6: "RCQR_EWORKSPACE", -7: "RCQR_EUNSUPPORTED"}
 
@@ -37,6 +37,7 @@ _SIGS = {
     "rcqr_sketch": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rcqr_small_qr": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rcqr_qrcp": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rcqr_srrqr": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rcqr_trsm": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _sz, _vp]),
     "rcqr_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp, _i64, _vp, _sz, _vp]),
     "rcqr_trsm_gram": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _sz,
@@ -161,6 +162,20 @@ def rcqr_qrcp(P, tau, colnorm2=None):
     return R, perm, rank, status
 
 
+def rcqr_srrqr(P, tau, f=1.5, colnorm2=None):
+    """Column pivoting followed by Gu-Eisenstat swaps with parameter f: (R, perm, rank, status)."""
+    k, n = P.shape
+    R = colmajor(n, n, torch.float64, P.device)
+    perm = torch.empty(n, dtype=torch.int32, device=P.device)
+    rank = torch.empty(1, dtype=torch.int64, device=P.device)
+    status = torch.zeros(2, dtype=torch.int32, device=P.device)
+    ws = _workspace(rcqr_workspace_size(max(k, 8), n, max(8, (k + 7) // 8 * 8), DIRECT, F64), P.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_srrqr", lib.rcqr_srrqr(_ptr(P), k, n, _ld(P), _ptr(colnorm2), float(tau), float(f), _ptr(R),
+                                        _ld(R), _ptr(perm), _ptr(rank), wp, wb, _ptr(status), _stream()))
+    return R, perm, rank, status
+
+
 def rcqr_trsm(X, R, perm=None, rank=None, Q=None, workspace=None):
     m, n = X.shape
     prec = prec_of(X.dtype)
@@ -219,7 +234,7 @@ def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=
         Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, dev)
     if R is None:
         R = colmajor(n, n, torch.float64, dev)
-    perm = torch.empty(n, dtype=torch.int32, device=dev) if variant in (RR, RR2) else None
+    perm = torch.empty(n, dtype=torch.int32, device=dev) if variant in (RR, RR2, SRR, SRR2) else None
     if rank is None:
         rank = torch.empty(1, dtype=torch.int64, device=dev)
     if status is None:
@@ -274,7 +289,7 @@ class Batch:
         self.prec = prec_of(Xs[0].dtype)
         dev = Xs[0].device
         qdt = torch.float64 if self.prec == F64 else torch.float32
-        rr = variant in (RR, RR2)
+        rr = variant in (RR, RR2, SRR, SRR2)
         self.Qs, self.Rs, self.perms, self.ranks = [], [], [], []
         self.status = torch.zeros((len(Xs), 2), dtype=torch.int32, device=dev)
         arr = (rcqr_problem * len(Xs))()

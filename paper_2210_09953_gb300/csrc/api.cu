@@ -111,7 +111,7 @@ int rcqr_theta_table(int32_t *out) {
 double rcqr_theta_scale(int64_t k) { return k > 0 ? theta_scale(k) : 0.0; }
 
 size_t rcqr_workspace_size(int64_t m, int64_t n, int64_t k, int variant, int prec) {
-  if (!valid_sizes(m, n, k) || !valid_prec(prec) || variant < 0 || variant > 3) return 0;
+  if (!valid_sizes(m, n, k) || !valid_prec(prec) || variant < 0 || variant > 5) return 0;
   Workspace w(nullptr, 0);
   FactorBuffers b;
   take_factor_buffers(w, n, k, b);
@@ -160,6 +160,22 @@ rcqr_status rcqr_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const 
   }
   return cuda_status(
       launch_qrcp(P, k, n, ldp, colnorm2, tau, R, ldr, perm, rank, dev_status, w, stream));
+}
+
+rcqr_status rcqr_srrqr(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
+                       double tau, double f, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
+                       void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  if (!P || !R || !perm || !rank || n < 1 || n > 256 || k < n || k > 2048 || ldp < k || ldr < n ||
+      !(tau >= 0.0) || !(f >= 1.0))
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < small_qr_workspace(k, n)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  if (dev_status) {
+    rcqr_status s = cuda_status(launch_reset_status(dev_status, stream));
+    if (s != RCQR_OK) return s;
+  }
+  return cuda_status(
+      launch_qrcp(P, k, n, ldp, colnorm2, tau, R, ldr, perm, rank, dev_status, w, stream, f));
 }
 
 rcqr_status rcqr_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
@@ -231,10 +247,12 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
   if (!X || !Q || !R || !dev_status || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m ||
-      ldq < m || ldr < n || variant < 0 || variant > 3)
+      ldq < m || ldr < n || variant < 0 || variant > 5)
     return RCQR_EINVAL;
-  const bool rr = variant == RCQR_RR || variant == RCQR_RR2;
-  const bool pass2 = variant == RCQR_DIRECT2 || variant == RCQR_RR2;
+  const bool rr = variant == RCQR_RR || variant == RCQR_RR2 || variant == RCQR_SRR || variant == RCQR_SRR2;
+  const bool pass2 = variant == RCQR_DIRECT2 || variant == RCQR_RR2 || variant == RCQR_SRR2;
+  // the strong-RRQR parameter f of Sec. 4 / Sec. 6.1 (0: column pivoting alone)
+  const double strong_f = (variant == RCQR_SRR || variant == RCQR_SRR2) ? kStrongRrqrF : 0.0;
   if (rr && (!perm || !(tau >= 0.0))) return RCQR_EINVAL;
   if (X == Q && (rr || elem_size(prec) != q_elem_size(prec) || ldx != ldq)) return RCQR_EINVAL;
   if (!workspace || !aligned(workspace) || ws_bytes < rcqr_workspace_size(m, n, k, variant, prec))
@@ -270,7 +288,7 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   } else {
     // Alg. 7 steps 2-3 and the de-normalisation R <- R Pi^T D Pi
     RCQR_TRY(launch_qrcp(b.P, k, n, k, b.colnorm2, tau, R, ldr, perm, rk, dev_status, *scratch(),
-                         stream));
+                         stream, strong_f));
     pm = perm;
     rkp = rk;
   }

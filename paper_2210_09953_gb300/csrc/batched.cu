@@ -122,13 +122,13 @@ bool valid_problem(const rcqr_problem &p, int variant, int prec) {
   if (!p.X || !p.Q || !p.R || !p.dev_status) return false;
   if (p.m < 1 || p.n < 1 || p.n > 256 || p.k < p.n || p.k > 2048 || (p.k % 8) != 0) return false;
   if (p.ldx < p.m || p.ldq < p.m || p.ldr < p.n) return false;
-  if ((variant == RCQR_RR || variant == RCQR_RR2) && !p.perm) return false;
+  if (rank_revealing_variant(variant) && !p.perm) return false;
   if (p.X == p.Q) return false;
   (void)prec;
   return true;
 }
 
-bool rank_revealing(int variant) { return variant == RCQR_RR || variant == RCQR_RR2; }
+bool rank_revealing(int variant) { return rank_revealing_variant(variant); }
 
 // Per-problem region of the rank-revealing phases: P (k x n), the squared column
 // norms (n) and the QRCP working copy, each 256-byte aligned.
@@ -197,11 +197,12 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
   }
   for (int c = 0; c < nlaunch; ++c) {
     const int b0 = c * kQrcpJobsPerLaunch, cnt = std::min(kQrcpJobsPerLaunch, count - b0);
-    if (launch_qrcp_jobs(jobs.data() + b0, cnt, tau, d->s[c % nb]) != cudaSuccess) return RCQR_ECUDA;
+    const double f = (variant == RCQR_SRR || variant == RCQR_SRR2) ? kStrongRrqrF : 0.0;
+    if (launch_qrcp_jobs(jobs.data() + b0, cnt, tau, d->s[c % nb], f) != cudaSuccess) return RCQR_ECUDA;
   }
   if (!fg.join()) return RCQR_ECUDA;
   // (C) substitution (Alg. 7 step 4) and, for RR2, one CholeskyQR pass (Alg. 3 steps 2-4)
-  const bool pass2 = variant == RCQR_RR2;
+  const bool pass2 = variant == RCQR_RR2 || variant == RCQR_SRR2;
   const int qprec = prec == RCQR_F64 ? RCQR_F64 : RCQR_F32;
   if (!fg.fork(ns)) return RCQR_ECUDA;
   for (int t = 0; t < count; ++t) {
@@ -284,8 +285,8 @@ size_t rcqr_batched_workspace_size(const rcqr_problem *probs, int count, int var
 
 rcqr_status rcqr_factor_batched(const rcqr_problem *probs, int count, int variant, int prec, double tau,
                                 void *workspace, size_t ws_bytes, cudaStream_t stream) {
-  if (!probs || count < 1 || variant < 0 || variant > 3 || !(prec >= 0 && prec <= 2)) return RCQR_EINVAL;
-  if ((variant == RCQR_RR || variant == RCQR_RR2) && !(tau >= 0.0)) return RCQR_EINVAL;
+  if (!probs || count < 1 || variant < 0 || variant > 5 || !(prec >= 0 && prec <= 2)) return RCQR_EINVAL;
+  if (rank_revealing_variant(variant) && !(tau >= 0.0)) return RCQR_EINVAL;
   for (int i = 0; i < count; ++i)
     if (!valid_problem(probs[i], variant, prec)) return RCQR_EINVAL;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return RCQR_EWORKSPACE;

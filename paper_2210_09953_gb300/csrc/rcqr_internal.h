@@ -57,6 +57,11 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
+// f of the strong rank-revealing QR in the RCQR_SRR / RCQR_SRR2 variants (Sec. 4, Sec. 6.1).
+constexpr double kStrongRrqrF = 1.5;
+
+inline bool rank_revealing_variant(int v) { return v == RCQR_RR || v == RCQR_RR2 || v == RCQR_SRR || v == RCQR_SRR2; }
+
 inline size_t elem_size(int prec) { return prec == RCQR_F64 ? 8 : (prec == RCQR_F32 ? 4 : 2); }
 inline size_t q_elem_size(int prec) { return prec == RCQR_F64 ? 8 : 4; }
 
@@ -93,9 +98,10 @@ cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, 
 // R only (diag >= 0) by a TSQR tree over several CTAs.
 cudaError_t launch_small_r(const double *P, int64_t k, int64_t n, int64_t ldp, double *R, int64_t ldr,
                            Workspace &ws, cudaStream_t st);
+// f > 0: the strong-RRQR swaps of Gu & Eisenstat with parameter f follow the pivoting.
 cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
                         double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
-                        int *dev_status, Workspace &ws, cudaStream_t st);
+                        int *dev_status, Workspace &ws, cudaStream_t st, double f = 0.0);
 // One QRCP of a batch (the arguments of launch_qrcp, gwork: qrcp_work_doubles(k, n) doubles).
 struct QrcpJob {
   const double *P;
@@ -112,7 +118,7 @@ struct QrcpJob {
 constexpr int kQrcpJobsPerLaunch = 128;
 size_t qrcp_work_doubles(int64_t k, int64_t n);
 // Up to kQrcpJobsPerLaunch QRCPs in one launch, one CTA each.
-cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st);
+cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st, double f = 0.0);
 // R' = chol(A[:r,:r]), R[:r,:] <- R' R[:r,:].
 cudaError_t launch_chol_update(const double *A, int64_t n, int64_t lda, const int64_t *rank,
                                double *Rp, int64_t ldrp, double *R, int64_t ldr, int *dev_status,
@@ -130,16 +136,18 @@ cudaError_t launch_set_rank(int64_t *rank, int64_t value, cudaStream_t st);
 
 // ---- bulk kernels over m -----------------------------------------------------
 size_t trsm_workspace(int64_t m, int64_t n, int prec);
+// allow_tc = false keeps the FP32 SIMT substitution (round-to-nearest operations
+// throughout) where the tensor-core kernel would otherwise be used.
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
                         void *Q, int64_t ldq, Workspace &ws, cudaStream_t st,
-                        int *dev_status = nullptr);
+                        int *dev_status = nullptr, bool allow_tc = true);
 // FP32 substitution and Gram of the mixed path (trsm_f32.cu).
 bool trsm32_supported(int64_t n);
 size_t trsm32_workspace(int64_t n);
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st, int *dev_status = nullptr);
+                          Workspace &ws, cudaStream_t st, int *dev_status = nullptr, bool allow_tc = true);
 int gram32_groups(int64_t m, int64_t n);
 cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
                           double *partial, int groups, cudaStream_t st);

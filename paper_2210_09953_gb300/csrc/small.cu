@@ -419,14 +419,183 @@ cluster_r_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, double
   }
 }
 
-// Column-pivoted QR of P D^{-1} + rank + de-normalised R.
+// Copy P[:, perm] D^{-1} (columns permuted and normalised) into A (lda).
+__device__ void load_permuted(const double *P, int64_t ldp, int k, int n, const int *perm, const double *Dc,
+                              double *A, int lda) {
+  for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
+    const int i = (int)(e % k), c = (int)(e / k);
+    const int src = perm[c];
+    A[i + (int64_t)c * lda] = P[i + (int64_t)src * ldp] / Dc[src];
+  }
+  __syncthreads();
+}
+
+// ||R||_2 (R n x n upper) by power iteration on R^T R from the all-ones vector, until the
+// estimate ||R x|| / ||x|| (non-decreasing) grows by at most 1e-13 of itself, at most 100
+// steps.  Every thread returns the estimate.
+__device__ double spectral_norm_est(const double *R, int64_t ldr, int n, double *s_x, double *s_y, double *s_t,
+                                    double *s_scal) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = 1.0;
+  __syncthreads();
+  double norm2 = 0.0;
+  for (int it = 0; it < 100; ++it) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // y = R x
+      double sacc = 0.0;
+      for (int c = i; c < n; ++c) sacc = fma(R[i + (int64_t)c * ldr], s_x[c], sacc);
+      s_y[i] = sacc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double yy = 0.0, xx = 0.0;
+      for (int c = threadIdx.x; c < n; c += 32) {
+        yy = fma(s_y[c], s_y[c], yy);
+        xx = fma(s_x[c], s_x[c], xx);
+      }
+      yy = warp0_sum(yy);
+      xx = warp0_sum(xx);
+      if (threadIdx.x == 0) s_scal[0] = xx > 0.0 ? sqrt(yy / xx) : 0.0;   // ||R x|| / ||x||
+    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {  // x' = R^T y
+      double sacc = 0.0;
+      for (int i = 0; i <= c; ++i) sacc = fma(R[i + (int64_t)c * ldr], s_y[i], sacc);
+      s_t[c] = sacc;
+    }
+    __syncthreads();
+    const double est = s_scal[0];
+    const bool done = it >= 2 && est - norm2 <= 1e-13 * est;
+    norm2 = est;
+    if (threadIdx.x < 32) {
+      double nn = 0.0;
+      for (int c = threadIdx.x; c < n; c += 32) nn = fma(s_t[c], s_t[c], nn);
+      nn = warp0_sum(nn);
+      if (threadIdx.x == 0) s_scal[1] = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = s_t[c] * s_scal[1];
+    __syncthreads();
+    if (done) break;
+  }
+  return norm2;
+}
+
+// Alg. 7 step 3: the least r with ||R[r:, r:]||_F <= tau ||R||_2 (thread 0; returned to all).
+__device__ int truncation_rank_dev(const double *R, int64_t ldr, int n, double tau, double norm2, double *s_y,
+                                   int *s_out) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double sacc = 0.0;
+    for (int c = i; c < n; ++c) sacc = fma(R[i + (int64_t)c * ldr], R[i + (int64_t)c * ldr], sacc);
+    s_y[i] = sacc;    // row i's share of the suffix Frobenius norms
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double bound = tau * norm2;
+    double suffix = 0.0;
+    int r = n;
+    // F2[r] = sum_{i >= r} s_y[i] is non-increasing in r
+    for (int rr = n; rr >= 0; --rr) {
+      if (rr < n) suffix += s_y[rr];
+      if (sqrt(suffix) <= bound) r = rr;
+      else break;
+    }
+    *s_out = r;
+  }
+  __syncthreads();
+  return *s_out;
+}
+
+// Strong-RRQR swaps (Gu & Eisenstat 1996, Algorithm 4) at rank r on the normalised R of
+// P[:, perm] D^{-1}: while the largest
+//   rho_ij = (R11^{-1} R12)_ij^2 + (gamma_j(R22) / omega_i(R11))^2
+// (gamma_j: 2-norm of column j of R22, omega_i: 1 / 2-norm of row i of R11^{-1}; the first
+// maximum in column-major order on ties) exceeds f^2, columns i and r + j trade places and
+// P[:, perm] D^{-1} is factored again by Householder QR.  sqrt(rho_ij) is the growth of
+// |det R11| under that swap, so the loop ends; at most 4 n swaps.  W (r n doubles of scratch)
+// holds R11^{-1} (r x r) and R11^{-1} R12 (r x (n - r)), both with leading dimension r.
+__device__ void strong_swaps(const double *P, int k, int n, int64_t ldp, double *R, int64_t ldr, double *A, int lda,
+                             double *W, int r, double f, int *s_perm, const double *s_D, double *s_w, double *s_g,
+                             double *s_beta, double *s_diag, unsigned long long *s_bkey, int *s_bidx) {
+  if (r <= 0 || r >= n) return;
+  const int nr = n - r;
+  double *Wi = W, *W12 = W + (int64_t)r * r;
+  for (int sw = 0; sw < 4 * n; ++sw) {
+    // columns of R11^{-1} and of R11^{-1} R12 by back substitution, one thread per column
+    for (int c = threadIdx.x; c < r + nr; c += blockDim.x) {
+      double *out = c < r ? Wi + (int64_t)c * r : W12 + (int64_t)(c - r) * r;
+      const int top = c < r ? c : r - 1;
+      for (int i = r - 1; i > top; --i) out[i] = 0.0;
+      for (int i = top; i >= 0; --i) {
+        double x = c < r ? (i == c ? 1.0 : 0.0) : R[i + (int64_t)c * ldr];
+        for (int t = i + 1; t <= top; ++t) x = fma(-R[i + (int64_t)t * ldr], out[t], x);
+        out[i] = x / R[i + (int64_t)i * ldr];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {     // 1 / omega_i^2
+      double sacc = 0.0;
+      for (int c = i; c < r; ++c) sacc = fma(Wi[i + (int64_t)c * r], Wi[i + (int64_t)c * r], sacc);
+      s_w[i] = sacc;
+    }
+    for (int j = threadIdx.x; j < nr; j += blockDim.x) {    // gamma_j^2
+      double sacc = 0.0;
+      for (int t = r; t <= r + j; ++t) sacc = fma(R[t + (int64_t)(r + j) * ldr], R[t + (int64_t)(r + j) * ldr], sacc);
+      s_g[j] = sacc;
+    }
+    __syncthreads();
+    unsigned long long best = 0;
+    int bidx = -1;
+    for (int t = threadIdx.x; t < r * nr; t += blockDim.x) {
+      const int i = t % r, j = t / r;
+      const double w = W12[i + (int64_t)j * r];
+      const double rho = fma(w, w, s_w[i] * s_g[j]);
+      const unsigned long long key = rho >= 0.0 ? (unsigned long long)__double_as_longlong(rho) : 0ull;
+      if (bidx < 0 || key > best) {    // t increases: on a tie the first (lowest) t stays
+        best = key;
+        bidx = t;
+      }
+    }
+    s_bkey[threadIdx.x] = best;
+    s_bidx[threadIdx.x] = bidx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long bk = 0;
+      int bt = -1;
+      for (int u = 0; u < (int)blockDim.x; ++u) {
+        const int t = s_bidx[u];
+        if (t < 0) continue;
+        if (bt < 0 || s_bkey[u] > bk || (s_bkey[u] == bk && t < bt)) {
+          bk = s_bkey[u];
+          bt = t;
+        }
+      }
+      const double rho = __longlong_as_double((long long)bk);
+      s_bidx[0] = (bt >= 0 && rho > f * f) ? bt : -1;
+      if (s_bidx[0] >= 0) {
+        const int i = bt % r, j = bt / r;
+        const int tmp = s_perm[i];
+        s_perm[i] = s_perm[r + j];
+        s_perm[r + j] = tmp;
+      }
+    }
+    __syncthreads();
+    if (s_bidx[0] < 0) break;
+    __syncthreads();
+    load_permuted(P, ldp, k, n, s_perm, s_D, A, lda);
+    for (int j = 0; j < n; ++j) householder_step(A, k, n, lda, j, s_beta, s_diag);
+    store_R(A, lda, n, s_diag, R, ldr);
+    __syncthreads();
+  }
+}
+
+// Column-pivoted QR of P D^{-1} + rank + de-normalised R; f > 0: followed by the
+// strong-RRQR swaps at the truncation rank (repeated while the rank of the swapped factor
+// changes, at most 4 rounds).
 __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2,
-                          double tau, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
-                          int *dev_status, double *gwork, int use_smem) {
+                          double tau, double f, double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out,
+                          int *dev_status, double *gwork, int use_smem, double *wscratch) {
   extern __shared__ double smem[];
   __shared__ double s_beta[256], s_diag[256], s_D[256], s_x[256], s_y[256], s_scal[4];
   __shared__ unsigned long long s_key[256];
-  __shared__ int s_perm[256];
+  __shared__ int s_perm[256], s_bidx[256];
   __shared__ int s_piv;
   double *A = use_smem ? smem : gwork;
   const int lda = odd_ld(k);
@@ -442,9 +611,9 @@ __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ld
     // non-negative doubles order like their bit patterns
     for (int c = j + threadIdx.x; c < n; c += blockDim.x) {
       const double *ac = A + (int64_t)c * lda;
-      double s = 0.0;
-      for (int i = j; i < k; ++i) s = fma(ac[i], ac[i], s);
-      s_key[c] = (unsigned long long)__double_as_longlong(sqrt(s));
+      double sacc = 0.0;
+      for (int i = j; i < k; ++i) sacc = fma(ac[i], ac[i], sacc);
+      s_key[c] = (unsigned long long)__double_as_longlong(sqrt(sacc));
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -488,68 +657,23 @@ __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ld
   }
   store_R(A, lda, n, s_diag, R, ldr);
   __syncthreads();
-  // ||R||_2 by 24 steps of power iteration on R^T R from the all-ones vector
-  for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = 1.0;
-  __syncthreads();
-  double norm2 = 0.0;
-  for (int it = 0; it < 24; ++it) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // y = R x
-      double s = 0.0;
-      for (int c = i; c < n; ++c) s = fma(R[i + (int64_t)c * ldr], s_x[c], s);
-      s_y[i] = s;
+  double norm2 = spectral_norm_est(R, ldr, n, s_x, s_y, s_beta, s_scal);
+  int r = truncation_rank_dev(R, ldr, n, tau, norm2, s_y, &s_piv);
+  if (f > 0.0) {
+    double *W = wscratch ? wscratch : A;       // A is reloaded after every swap decision
+    for (int round = 0; round < 4 && r > 0 && r < n; ++round) {
+      strong_swaps(P, k, n, ldp, R, ldr, A, lda, W, r, f, s_perm, s_D, s_x, s_y, s_beta, s_diag, s_key, s_bidx);
+      norm2 = spectral_norm_est(R, ldr, n, s_x, s_y, s_beta, s_scal);
+      const int r2 = truncation_rank_dev(R, ldr, n, tau, norm2, s_y, &s_piv);
+      if (r2 == r) break;
+      r = r2;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double yy = 0.0, xx = 0.0;
-      for (int c = threadIdx.x; c < n; c += 32) {
-        yy = fma(s_y[c], s_y[c], yy);
-        xx = fma(s_x[c], s_x[c], xx);
-      }
-      yy = warp0_sum(yy);
-      xx = warp0_sum(xx);
-      if (threadIdx.x == 0) s_scal[0] = xx > 0.0 ? sqrt(yy / xx) : 0.0;   // ||R x|| / ||x||
-    }
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {  // x' = R^T y
-      double s = 0.0;
-      for (int i = 0; i <= c; ++i) s = fma(R[i + (int64_t)c * ldr], s_y[i], s);
-      s_beta[c] = s;
-    }
-    __syncthreads();
-    norm2 = s_scal[0];
-    if (threadIdx.x < 32) {
-      double nn = 0.0;
-      for (int c = threadIdx.x; c < n; c += 32) nn = fma(s_beta[c], s_beta[c], nn);
-      nn = warp0_sum(nn);
-      if (threadIdx.x == 0) s_scal[1] = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n; c += blockDim.x) s_x[c] = s_beta[c] * s_scal[1];
-    __syncthreads();
   }
-  // suffix Frobenius norms: F2[r] = sum_{i>=r} sum_{c>=i} R_ic^2
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double s = 0.0;
-    for (int c = i; c < n; ++c) s = fma(R[i + (int64_t)c * ldr], R[i + (int64_t)c * ldr], s);
-    s_y[i] = s;
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    const double bound = tau * norm2;
-    double suffix = 0.0;
-    int r = n;
-    // the least r with sqrt(F2[r]) <= bound; F2 is non-increasing in r
-    for (int rr = n; rr >= 0; --rr) {
-      if (rr < n) suffix += s_y[rr];
-      if (sqrt(suffix) <= bound) r = rr;
-      else break;
-    }
-    s_piv = r;
     *rank_out = r;
     // the first error of a call is kept (an earlier one, e.g. a timed-out sketch, wins)
     if (r == 0 && dev_status && atomicCAS(dev_status, 0, (int)RCQR_ERANK0) == 0) dev_status[1] = -1;
   }
-  __syncthreads();
-  const int r = s_piv;
   for (int c = threadIdx.x; c < n; c += blockDim.x) perm_out[c] = s_perm[c];
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e % n, c = e / n;
@@ -559,9 +683,11 @@ __device__ void qrcp_body(const double *__restrict__ P, int k, int n, int64_t ld
 }
 
 __global__ void __launch_bounds__(kSmallThreads)
-qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2, double tau, double *R,
-            int64_t ldr, int32_t *perm_out, int64_t *rank_out, int *dev_status, double *gwork, int use_smem) {
-  qrcp_body(P, k, n, ldp, colnorm2, tau, R, ldr, perm_out, rank_out, dev_status, gwork, use_smem);
+qrcp_kernel(const double *__restrict__ P, int k, int n, int64_t ldp, const double *colnorm2, double tau, double f,
+            double *R, int64_t ldr, int32_t *perm_out, int64_t *rank_out, int *dev_status, double *gwork, int use_smem) {
+  // the swap scratch shares gwork when the working copy lives in shared memory
+  qrcp_body(P, k, n, ldp, colnorm2, tau, f, R, ldr, perm_out, rank_out, dev_status, gwork, use_smem,
+            use_smem ? gwork : nullptr);
 }
 
 // Many QRCPs in one launch (a batch of factorizations): CTA b runs job b, with its
@@ -571,10 +697,11 @@ struct QrcpJobs {
 };
 
 __global__ void __launch_bounds__(kSmallThreads)
-qrcp_batched_kernel(const __grid_constant__ QrcpJobs jobs, double tau, int64_t smem_doubles) {
+qrcp_batched_kernel(const __grid_constant__ QrcpJobs jobs, double tau, double f, int64_t smem_doubles) {
   const QrcpJob &jb = jobs.j[blockIdx.x];
   const bool sm = (int64_t)odd_ld(jb.k) * jb.n <= smem_doubles;
-  qrcp_body(jb.P, jb.k, jb.n, jb.ldp, jb.colnorm2, tau, jb.R, jb.ldr, jb.perm, jb.rank, jb.status, jb.gwork, sm);
+  qrcp_body(jb.P, jb.k, jb.n, jb.ldp, jb.colnorm2, tau, f, jb.R, jb.ldr, jb.perm, jb.rank, jb.status, jb.gwork, sm,
+            sm ? jb.gwork : nullptr);
 }
 
 // R' = chol(A[:r,:r]) (Alg. 3 step 3) on one CTA: left-looking on a shared-memory
@@ -796,20 +923,20 @@ cudaError_t launch_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, 
 
 cudaError_t launch_qrcp(const double *P, int64_t k, int64_t n, int64_t ldp, const double *colnorm2,
                         double tau, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
-                        int *dev_status, Workspace &ws, cudaStream_t st) {
+                        int *dev_status, Workspace &ws, cudaStream_t st, double f) {
   const bool sm = fits_smem(k, n);
   double *g = ws.take<double>((size_t)(k | 1) * n);
   if (!g) return cudaErrorMemoryAllocation;
   const size_t bytes = sm ? copy_bytes(k, n) : 0;
   if (sm) set_smem(qrcp_kernel, (int)kSmemLimit);
-  qrcp_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, colnorm2, tau, R, ldr, perm,
+  qrcp_kernel<<<1, kSmallThreads, bytes, st>>>(P, (int)k, (int)n, ldp, colnorm2, tau, f, R, ldr, perm,
                                                rank, dev_status, g, sm);
   return cudaGetLastError();
 }
 
 size_t qrcp_work_doubles(int64_t k, int64_t n) { return (size_t)(k | 1) * n; }
 
-cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st) {
+cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStream_t st, double f) {
   if (count < 1 || count > kQrcpJobsPerLaunch) return cudaErrorInvalidValue;
   QrcpJobs pj;
   int64_t need = 0;
@@ -823,7 +950,7 @@ cudaError_t launch_qrcp_jobs(const QrcpJob *jobs, int count, double tau, cudaStr
     cudaError_t e = set_smem(qrcp_batched_kernel, (int)kBatchedSmem);
     if (e != cudaSuccess) return e;
   }
-  qrcp_batched_kernel<<<count, kSmallThreads, (size_t)need * 8, st>>>(pj, tau, need);
+  qrcp_batched_kernel<<<count, kSmallThreads, (size_t)need * 8, st>>>(pj, tau, f, need);
   return cudaGetLastError();
 }
 

@@ -550,13 +550,13 @@ size_t trsm32_workspace(int64_t n) {
 
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st, int *dev_status) {
+                          Workspace &ws, cudaStream_t st, int *dev_status, bool allow_tc) {
   const int NB = trsm32_nb(n);
   float *Rf = ws.take<float>((size_t)NB * NB);
   float *dinv = ws.take<float>((size_t)NB);
   if (!Rf || !dinv) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
-  if (trsm_tc_supported(n))
+  if (allow_tc && trsm_tc_supported(n))
     return launch_trsm_tc(X, m, n, ldx, prec, Rf, dinv, perm, rank, (float *)Q, ldq, nullptr, dev_status, st);
   if (n > 64) {
     const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);

@@ -1,30 +1,36 @@
-// Q = X R^{-1} (Alg. 2 step 3 / Alg. 3 step 4) for 32 < n <= 64 as a blocked
-// substitution on the tcgen05 tensor cores, optionally fused with the Gram
-// matrix A = Q^T Q of the second pass (Alg. 3 step 2).
+// Q = X R^{-1} (Alg. 2 step 3) for 32 < n <= 64 as a blocked substitution on
+// the tcgen05 tensor cores, optionally fused with the Gram matrix A = Q^T Q of
+// the second pass (Alg. 3 step 2).
 //
 // A CTA of 128 threads takes tiles of 128 rows (thread t owns row t of the tile
-// and TMEM lane t).  The 64 (padded) columns form four blocks of 16.  For block
-// J the thread forms y_J = x_J - (sum_{I<J} q_I R_{I,J}) and solves the 16 x 16
-// triangular system y_J = q_J R_{J,J} by substitution in FP32 registers (the
-// diagonal block is never inverted).  The off-diagonal products run on the
-// tensor cores, right-looking: once block J is solved, its q_J is split exactly
-// into three bf16 pieces q = h + m + l (8 significant bits each, RN, so the sum
-// is exact for an FP32 q), and one group of MMAs adds q_J R_{J,>J} into the FP32
-// TMEM accumulator of the later columns.  R (rounded to FP32 once) is split the
-// same way; the six products with piece indices summing to at most two are kept
-// (h Rh, h Rm, m Rh, h Rl, m Rm, l Rh; the dropped ones are below 2^-26 of
-// |q||R|), so each update carries the error of an FP32 product sum -- the
-// row-wise backward error stays that of the FP32 substitution,
+// and TMEM lane t); the next tile's X is copied into shared memory (cp.async)
+// while the current one is processed.  The 64 (padded) columns form four blocks
+// of 16.  For block J the thread forms y_J = x_J - (sum_{I<J} q_I R_{I,J}) and
+// solves the 16 x 16 triangular system y_J = q_J R_{J,J} by substitution in
+// FP32 registers (the diagonal block is never inverted).  The off-diagonal
+// products run on the tensor cores, right-looking: once block J is solved, its
+// q_J is split exactly into three bf16 pieces q = h + m + l (8 significant bits
+// each, RN: the sum is exact for an FP32 q), and one group of MMAs adds
+// q_J R_{J,>J} into the FP32 TMEM accumulator of the later columns.  R (rounded
+// to FP32 once) is split the same way; the six products with piece indices
+// summing to at most two are kept (the dropped ones are below 2^-26 of
+// |q||R|), so each update carries the error of an FP32 sum of products, and
+// the row-wise backward error stays that of the FP32 substitution,
 // Q (R + dR) = X with |dR| <= c n u |R|, u = 2^-24 (Higham Thm. 8.5).
 //
-// The Gram (GRAM = true) reads the same slice buffer as the transposed (MN-major)
-// operand: per tile, A = [h; m]^T times B = [h | m] (FP32 in TMEM, restarted at
-// every tile) gives (h,h) + (h,m) in lanes 0..63 and (m,h) + (m,m) in lanes
-// 64..127; their tile sums are folded into per-thread FP32 Kahan accumulators.
-// The small terms [h; m]^T l accumulate in TMEM across all tiles (they are 2^-9
-// of the leading ones, so their FP32 rounding is negligible); their transposes
-// supply l^T h and l^T m.  The per-CTA partials go to FP64 and are summed in a
-// fixed order by the Gram reduction.
+// The Gram (GRAM = true) is formed from a second split of the finished rows,
+// read by the tensor cores as the transposed (MN-major) operand: per tile and
+// column c, h = an 8-bit fixed-point digit of q relative to the column's largest
+// |q| in the tile (h = round(q 2^(6-e)) 2^(e-6), e = floor(log2 max |q|)), then
+// m = RN_bf16(q - h), l = RN_bf16(q - h - m).  Every h_i h_j is an integer
+// multiple of 2^(e_i + e_j - 12) below 2^14 of them, so the 128-row sums of the
+// leading term (h,h) are exact in the FP32 accumulator whatever its rounding;
+// the other terms are at most 2^-8 of it.  Per tile, A = [h; m]^T times
+// B = [h | m] gives (h,h) + (h,m) in lanes 0..63 and (m,h) + (m,m) in lanes
+// 64..127, folded into per-thread FP32 Kahan sums; [h; m]^T l (2^-16 of the
+// leading term) accumulates in TMEM across the tiles and its transpose supplies
+// l^T h and l^T m.  The per-CTA partials go to FP64 and are summed in a fixed
+// order by the Gram reduction.
 #include <algorithm>
 
 #include "common.cuh"
@@ -39,7 +45,7 @@ constexpr int kTR = 128;            // rows per tile = TMEM lanes = threads per 
 constexpr int kTN = 64;             // padded columns (four blocks of 16)
 constexpr int kRSlice = kTN * kTN * 2;          // one bf16 slice of R: 8 KiB
 constexpr uint32_t kRSBO = (kTN / 8) * 128;     // R slice: 8-column groups 1 KiB apart
-constexpr uint32_t kWaitPollsTc = 1u << 22;
+constexpr uint32_t kWaitRounds = 1u << 20;      // bounded waits: rounds of try_wait (<= 1 us each)
 
 template <bool GRAM>
 struct TcCfg {
@@ -50,12 +56,8 @@ struct TcCfg {
   static constexpr uint32_t NCOLS = GRAM ? 256u : 64u;   // TMEM: update acc (48) [+ P 128 + L 64]
   static constexpr uint32_t P_COL = 64;
   static constexpr uint32_t L_COL = 192;
-  static constexpr int USED = Q_BYTES + 3 * kRSlice + 4 * 16 * 16 * 4 + 64 * 4 + 64 * 4 + 64;
-  // The Gram's transposed reads span at most 14 QSBO + 2048 + 16 QSBO + 128 bytes of the
-  // allocation whichever of its two strides the descriptor applies along K: the allocation
-  // covers that, so every tensor-core read stays inside this CTA's shared memory.
-  static constexpr int SPAN = GRAM ? 30 * (int)QSBO + 2048 + 128 : 0;
-  static constexpr int SMEM = USED > SPAN ? USED : SPAN;
+  static constexpr int X_BYTES = kTR * kTN * 4;     // the prefetched X tile (column-major)
+  static constexpr int SMEM = Q_BYTES + 3 * kRSlice + X_BYTES + 4 * 16 * 16 * 4 + 3 * 64 * 4 + 4 * 64 * 4 + 64;
 };
 
 struct TcTrsmArgs {
@@ -71,6 +73,7 @@ struct TcTrsmArgs {
   int64_t ldq;
   double *partial;      // GRAM: one n x n FP64 partial per CTA
   int *status;          // nullable: RCQR_ETIMEOUT on a wait that gave up
+  int vec;              // X's columns start on 16-byte boundaries at every tile: cp.async prefetch
 };
 
 __device__ __forceinline__ float to_f32v(float x) { return x; }
@@ -89,38 +92,79 @@ __device__ __forceinline__ void split3(float x0, float x1, uint32_t &h, uint32_t
   l = *reinterpret_cast<const uint32_t *>(&lb);
 }
 
+// The Gram split of two FP32 values: h = round(x sc) isc (an exact fixed-point digit,
+// sc = 2^(6-e), isc = 2^(e-6), or 0 when sc = 0), then m and l as in split3.
+__device__ __forceinline__ void split_fixed(float x0, float x1, float sc0, float sc1, float isc0, float isc1,
+                                            uint32_t &h, uint32_t &mm, uint32_t &l) {
+  const float h0 = rintf(x0 * sc0) * isc0, h1 = rintf(x1 * sc1) * isc1;
+  const __nv_bfloat162 hb = __floats2bfloat162_rn(h0, h1);     // exact: at most 8 significant bits
+  const float r0 = x0 - h0, r1 = x1 - h1;
+  const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
+  const float2 mf = __bfloat1622float2(mb);
+  const __nv_bfloat162 lb = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+  h = *reinterpret_cast<const uint32_t *>(&hb);
+  mm = *reinterpret_cast<const uint32_t *>(&mb);
+  l = *reinterpret_cast<const uint32_t *>(&lb);
+}
+
 // tcgen05 instruction descriptor, kind::f16, BF16 x BF16 -> FP32, both operands MN-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
   return umma::idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
+// Bounded wait on an mbarrier phase (try_wait rounds, each suspending for at most ~1 us);
+// gives up at once when another thread of the CTA already gave up.
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, int *fail) {
-  if (*(volatile int *)fail) return false;
-  uint32_t ns = 32;
-  for (uint32_t it = 0; it < kWaitPollsTc; ++it) {
-    if (umma::mbar_wait(bar, parity, 1)) return true;
+  for (uint32_t it = 0; it < kWaitRounds; ++it) {
     if (*(volatile int *)fail) return false;
-    __nanosleep(ns);
-    ns = ns < 256 ? ns * 2 : 256;
+    if (umma::mbar_try_wait_hint(bar, parity, 1000)) return true;
   }
   *(volatile int *)fail = 1;
   return false;
 }
 
+__device__ __forceinline__ void cp_async16_zf(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+// Starts the copy of tile `tile`'s X rows (columns Src[c]; -1: zeros) into Xs, column-major
+// (column c at Xs + c * 128 elements); rows beyond m are zero-filled.
+template <class TX>
+__device__ __forceinline__ void prefetch_x(const TX *X, int64_t m, int64_t ldx, int64_t tile, const int *Src,
+                                           unsigned char *Xs) {
+  constexpr int EPC = 16 / (int)sizeof(TX);          // elements per 16-byte chunk
+  constexpr int CPC = kTR / EPC;                     // chunks per column
+  const int64_t row0 = tile * kTR;
+  for (int ch = threadIdx.x; ch < kTN * CPC; ch += kTR) {
+    const int c = ch / CPC, part = ch % CPC;
+    const int src = Src[c];
+    const int64_t r = row0 + (int64_t)part * EPC;
+    const int64_t left = m - r;
+    const int valid = (src >= 0 && left > 0) ? (int)(left < EPC ? left : EPC) : 0;
+    const TX *g = valid > 0 ? X + r + (int64_t)src * ldx : X;
+    cp_async16_zf(Xs + ((size_t)c * kTR + (size_t)part * EPC) * sizeof(TX), g, valid * (int)sizeof(TX));
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <class TX, bool GRAM>
-__global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a) {
+__global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
   using C = TcCfg<GRAM>;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *Qs = smem;                                   // slice buffer, K-major core matrices
   unsigned char *Rs = Qs + C::Q_BYTES;                        // 3 slices of R (B operands)
-  float *Rd = reinterpret_cast<float *>(Rs + 3 * kRSlice);    // diagonal blocks, Rd[J][c][i]
+  unsigned char *Xs = Rs + 3 * kRSlice;                       // the prefetched X tile
+  float *Rd = reinterpret_cast<float *>(Xs + C::X_BYTES);     // diagonal blocks, Rd[J][c][i]
   float *Ds = Rd + 4 * 256;                                   // fl32(1 / R_jj)
-  int *Src = reinterpret_cast<int *>(Ds + 64);                // source column of X per column
+  float *Sc = Ds + 64, *Isc = Sc + 64;                        // Gram split scales per column
+  unsigned *Wmax = reinterpret_cast<unsigned *>(Isc + 64);    // per-warp column maxima (4 x 64)
+  int *Src = reinterpret_cast<int *>(Wmax + 4 * 64);          // source column of X per column
   __shared__ uint64_t bar_upd, bar_gram, bar_drain;
   __shared__ uint32_t tslot;
   __shared__ int s_fail;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TX *X = static_cast<const TX *>(a.X);
   const int r = a.rank ? (int)(*a.rank < (int64_t)a.n ? *a.rank : (int64_t)a.n) : a.n;
 
@@ -166,10 +210,11 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
   bool gram_pending = false;
   const int64_t tiles = (a.m + kTR - 1) / kTR;
   const uint32_t row_sw = (uint32_t)(tid / 8) * C::QSBO + (uint32_t)(tid % 8) * 16;   // this row's core offset
+  if (a.vec && (int64_t)blockIdx.x < tiles) prefetch_x<TX>(X, a.m, a.ldx, blockIdx.x, Src, Xs);
 
   // folds the finished Gram MMAs of the previous tile (TMEM P region) into the Kahan sums
   auto fold = [&]() {
-    if (!wait_bar(&bar_gram, ph_gram, &s_fail)) { /* gave up: the sums are discarded */ }
+    wait_bar(&bar_gram, ph_gram, &s_fail);   // on a timeout the sums are discarded below
     ph_gram ^= 1u;
     umma::fence_after_sync();
 #pragma unroll
@@ -199,10 +244,18 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
       gram_pending = false;
     }
     float q[kTN];
+    if (a.vec) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+      const TX *xs = reinterpret_cast<const TX *>(Xs);
 #pragma unroll
-    for (int j = 0; j < kTN; ++j) {
-      const int src = Src[j];
-      q[j] = (live && src >= 0) ? to_f32v(X[row + (int64_t)src * a.ldx]) : 0.0f;
+      for (int j = 0; j < kTN; ++j) q[j] = to_f32v(xs[j * kTR + tid]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kTN; ++j) {
+        const int src = Src[j];
+        q[j] = (live && src >= 0) ? to_f32v(X[row + (int64_t)src * a.ldx]) : 0.0f;
+      }
     }
 #pragma unroll
     for (int J = 0; J < 4; ++J) {
@@ -226,7 +279,7 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
         for (int i = 0; i < c; ++i) s = fmaf(-q[16 * J + i], rd[16 * c + i], s);
         q[16 * J + c] = s * Ds[16 * J + c];
       }
-      if (J < 3 || GRAM) {
+      if (J < 3) {
         // the exact three-way split of q_J into the slice buffer (two 16-byte chunks per piece)
 #pragma unroll
         for (int h8 = 0; h8 < 2; ++h8) {
@@ -238,11 +291,11 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
           *reinterpret_cast<uint4 *>(Qs + row_sw + ((1 * C::CW + col) / 8) * 128) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
           *reinterpret_cast<uint4 *>(Qs + row_sw + ((2 * C::CW + col) / 8) * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-      }
-      if (J < 3) {
         umma::fence_proxy_async();
         umma::fence_before_sync();
         __syncthreads();
+        if (J == 0 && a.vec && tile + gridDim.x < tiles)   // Xs has been read by every thread
+          prefetch_x<TX>(X, a.m, a.ldx, tile + gridDim.x, Src, Xs);
         if (tid == 0 && !*(volatile int *)&s_fail) {
           umma::fence_after_sync();
           const int N = 16 * (3 - J);
@@ -269,6 +322,35 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
         if (j < n) a.Q[row + (int64_t)j * ldq] = q[j];
     }
     if constexpr (GRAM) {
+      // per column, the tile's largest |q| (magnitude bits order like the values)
+#pragma unroll
+      for (int j = 0; j < kTN; ++j) {
+        const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(q[j]) & 0x7FFFFFFFu);
+        if (lane == 0) Wmax[warp * 64 + j] = mx;
+      }
+      __syncthreads();
+      if (tid < kTN) {
+        const unsigned mx = max(max(Wmax[tid], Wmax[64 + tid]), max(Wmax[128 + tid], Wmax[192 + tid]));
+        const int be = (int)(mx >> 23);           // biased exponent of the largest |q|
+        // 2^(6 - e) and 2^(e - 6), e = be - 127; tiny or zero columns keep h = 0 (all in m, l)
+        const bool ok = be >= 40 && be <= 200;
+        Sc[tid] = ok ? __uint_as_float((uint32_t)(127 + 133 - be) << 23) : 0.0f;
+        Isc[tid] = ok ? __uint_as_float((uint32_t)(be - 6) << 23) : 0.0f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c8 = 0; c8 < kTN / 8; ++c8) {
+        uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int j = 8 * c8 + 2 * p;
+          split_fixed(q[j], q[j + 1], Sc[j], Sc[j + 1], Isc[j], Isc[j + 1], hw[p], mw[p], lw[p]);
+        }
+        const uint32_t col = 8 * c8;
+        *reinterpret_cast<uint4 *>(Qs + row_sw + ((0 * C::CW + col) / 8) * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(Qs + row_sw + ((1 * C::CW + col) / 8) * 128) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        *reinterpret_cast<uint4 *>(Qs + row_sw + ((2 * C::CW + col) / 8) * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
       umma::fence_proxy_async();
       umma::fence_before_sync();
       __syncthreads();
@@ -331,16 +413,19 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
     }
     __syncthreads();
     double *pb = a.partial + (int64_t)blockIdx.x * n * n;
+    const double nan = __longlong_as_double(0x7FF8000000000000ll);
+    const bool failed = *(volatile int *)&s_fail != 0;
     for (int e = tid; e < n * n; e += kTR) {
       const int ii = e % n, jj = e / n;
-      pb[e] = (ii <= jj) ? F[ii * 64 + jj] : 0.0;
+      pb[e] = failed ? nan : ((ii <= jj) ? F[ii * 64 + jj] : 0.0);
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 
   // drain: every MMA issued by thread 0 has finished before TMEM is released
   if (tid == 0) {
     umma::mma_commit(&bar_drain);
-    if (!umma::mbar_wait(&bar_drain, 0u, kWaitPollsTc)) s_fail = 1;
+    if (!umma::mbar_wait(&bar_drain, 0u, 1u << 22)) s_fail = 1;
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -352,7 +437,8 @@ __global__ void __launch_bounds__(kTR, GRAM ? 2 : 3) trsm_tc_kernel(TcTrsmArgs a
 template <bool GRAM>
 int tc_grid(int64_t m) {
   const int64_t tiles = (m + kTR - 1) / kTR;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)(GRAM ? 2 : 3) * num_sms()));
+  // two CTAs per SM (shared memory: slice buffer, R pieces and the X tile)
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)2 * num_sms()));
 }
 
 template <class TX, bool GRAM>
@@ -373,7 +459,10 @@ int trsm_tc_gram_groups(int64_t m) { return tc_grid<true>(m); }
 cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
                            const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
                            double *partial, int *status, cudaStream_t st) {
-  TcTrsmArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial, status};
+  const size_t es = prec == RCQR_BF16 ? 2 : 4;
+  // every 16-byte chunk of a tile column starts on a 16-byte boundary
+  const int vec = ((uintptr_t)X % 16 == 0) && ((size_t)ldx * es) % 16 == 0;
+  TcTrsmArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial, status, vec};
   const bool gram = partial != nullptr;
   if (gram) {
     const int grid = tc_grid<true>(m);

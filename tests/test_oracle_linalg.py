@@ -141,3 +141,70 @@ def test_forward_substitution_f32_backward_error_and_exact_case():
     Ri = np.triu(rng.integers(-3, 4, (8, 8)).astype(np.float64), 1) + np.eye(8)
     Qi = rng.integers(-5, 6, (50, 8)).astype(np.float64)
     assert np.array_equal(linalg.forward_substitution_f32(Qi @ Ri, Ri).astype(np.float64), Qi)
+
+
+def kahan(n, theta=1.2, pert=1e-10):
+    """The Kahan matrix diag(1, s, .., s^{n-1}) (I - c U), U strictly upper all-ones (every
+    trailing column norm is s^t at step t), with column j scaled by (1 - pert j) so that
+    column pivoting keeps the natural order."""
+    c, s = np.cos(theta), np.sin(theta)
+    K = np.triu(-c * np.ones((n, n)), 1) + np.eye(n)
+    K = np.diag(s ** np.arange(n)) @ K
+    return K * (1 - pert * np.arange(n))[None, :]
+
+
+def test_swap_ratio_is_the_determinant_growth_of_a_swap():
+    # Gu & Eisenstat Lemma 3.1: sqrt(rho_ij) = |det R11'| / |det R11| after columns i and r + j
+    # trade places; det R11' from numpy's QR of the swapped matrix (a library routine)
+    rng = np.random.default_rng(11)
+    P = rng.standard_normal((14, 6)) @ np.diag([3, 1, 0.5, 0.2, 1e-2, 1e-3])
+    _, R = linalg.householder_qr(P)
+    for r in range(1, 6):
+        rho = linalg.swap_ratios(R, r)
+        d0 = abs(np.prod(np.diag(R)[:r]))
+        for i in range(r):
+            for j in range(6 - r):
+                perm = np.arange(6)
+                perm[[i, r + j]] = perm[[r + j, i]]
+                _, Rs = np.linalg.qr(P[:, perm])
+                d1 = abs(np.prod(np.diag(Rs)[:r]))
+                assert abs(np.sqrt(rho[i, j]) - d1 / d0) <= 1e-10 * max(1.0, d1 / d0)
+
+
+def test_strong_rrqr_fixes_the_kahan_matrix():
+    n, r, f = 24, 23, 1.5
+    P = np.vstack([kahan(n), np.zeros((8, n))])
+    S0, R0, perm0 = linalg.qrcp(P)
+    assert perm0.tolist() == list(range(n))                        # no pivoting on Kahan's matrix
+    assert np.max(linalg.swap_ratios(R0, r)) > f * f               # ... and it is not a strong RRQR
+    S, R, perm, swaps = linalg.strong_rrqr_swaps(P, perm0, r, f)
+    assert swaps >= 1
+    assert np.max(linalg.swap_ratios(R, r)) <= f * f
+    # Gu-Eisenstat Thm 3.2 with q(r, n) = sqrt(1 + f^2 r (n - r))
+    sv = np.linalg.svd(P, compute_uv=False)
+    q = np.sqrt(1 + f * f * r * (n - r))
+    assert np.linalg.svd(R[:r, :r], compute_uv=False).min() >= sv[r - 1] / q * (1 - 1e-10)
+    assert np.linalg.norm(R[r:, r:], 2) <= sv[r] * q * (1 + 1e-10)
+    # a valid QR of the permuted matrix
+    assert np.allclose(S @ R, P[:, perm], atol=1e-13)
+    assert np.linalg.norm(S.T @ S - np.eye(n)) <= 1e-13
+    assert np.all(np.diag(R) >= 0) and np.array_equal(R, np.triu(R))
+    assert sorted(perm.tolist()) == list(range(n))
+
+
+def test_strong_rrqr_rank_and_local_maximality():
+    rng = np.random.default_rng(5)
+    m, n, r = 60, 9, 5
+    B = rng.standard_normal((m, r))
+    P = np.hstack([B, B @ rng.standard_normal((r, n - r)) + 1e-9 * rng.standard_normal((m, n - r))])
+    P = P[:, rng.permutation(n)]
+    S, R, perm, rk = linalg.strong_rrqr(P, 1e-6, 1.5)
+    assert rk == r
+    # no single swap grows |det R11| by more than f (brute force over all swaps)
+    d0 = abs(np.prod(np.diag(R)[:r]))
+    for i in range(r):
+        for j in range(n - r):
+            pp = perm.copy()
+            pp[[i, r + j]] = pp[[r + j, i]]
+            _, Rs = np.linalg.qr(P[:, pp])
+            assert abs(np.prod(np.diag(Rs)[:r])) <= 1.5 * d0 * (1 + 1e-9)
