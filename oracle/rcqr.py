@@ -21,33 +21,36 @@ sums are added in order.
 import numpy as np
 
 from . import linalg
-from .theta import theta_levels, theta_scale
+from . import theta as _theta
+from .theta import GAUSSIAN, theta_levels, theta_scale
 
 SKETCH_ROW_BLOCK = 1 << 14
 
 
-def sketch(X, k, seed, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK):
+def sketch(X, k, seed, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK, dist=GAUSSIAN):
     """P = Theta X (k x n, FP64), Theta rows for global X rows row_offset .. row_offset+m-1 (Alg. 2 step 1)."""
     X = np.asarray(X, dtype=np.float64)
     m, n = X.shape
     acc = np.zeros((k, n))
     for r0 in range(0, m, row_block):
         r1 = min(m, r0 + row_block)
-        G = theta_levels(seed, k, row_offset + r0, r1 - r0, stream)
+        G = (theta_levels(seed, k, row_offset + r0, r1 - r0, stream) if dist == GAUSSIAN
+             else _theta.levels(seed, k, row_offset + r0, r1 - r0, stream, dist=dist))
         acc += G @ X[r0:r1]
-    return theta_scale(k) * acc
+    return (theta_scale(k) if dist == GAUSSIAN else _theta.scale(k, dist)) * acc
 
 
-def sketch_rows(X, k, seed, rows, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK):
+def sketch_rows(X, k, seed, rows, row_offset=0, stream=0, row_block=SKETCH_ROW_BLOCK, dist=GAUSSIAN):
     """Selected rows of P = Theta X (one output row at a time for sampled checks of long X)."""
     X = np.asarray(X)
     m, n = X.shape
     acc = np.zeros((len(rows), n))
     for r0 in range(0, m, row_block):
         r1 = min(m, r0 + row_block)
-        G = theta_levels(seed, k, row_offset + r0, r1 - r0, stream, rows=rows)
+        G = (theta_levels(seed, k, row_offset + r0, r1 - r0, stream, rows=rows) if dist == GAUSSIAN
+             else _theta.levels(seed, k, row_offset + r0, r1 - r0, stream, rows=rows, dist=dist))
         acc += G @ np.asarray(X[r0:r1], dtype=np.float64)
-    return theta_scale(k) * acc
+    return (theta_scale(k) if dist == GAUSSIAN else _theta.scale(k, dist)) * acc
 
 
 def column_norms(X):
@@ -63,9 +66,9 @@ def rcholqr_from_sketch(X, P):
     return Q, S, R
 
 
-def rcholqr(X, k, seed, stream=0):
+def rcholqr(X, k, seed, stream=0, dist=GAUSSIAN):
     """Alg. 2: returns (Q, S, R)."""
-    P = sketch(X, k, seed, stream=stream)
+    P = sketch(X, k, seed, stream=stream, dist=dist)
     return rcholqr_from_sketch(X, P)
 
 
@@ -84,9 +87,9 @@ def cholqr_pass(Q, R):
     return linalg.forward_substitution(Q, Rp), Rp @ R, Rp
 
 
-def rcholqr2(X, k, seed, stream=0):
+def rcholqr2(X, k, seed, stream=0, dist=GAUSSIAN):
     """Alg. 3: returns (Q, R, S) -- S is the orthonormal sketch from the first pass."""
-    Q, S, R = rcholqr(X, k, seed, stream)
+    Q, S, R = rcholqr(X, k, seed, stream, dist)
     Q2, R2, _ = cholqr_pass(Q, R)
     return Q2, R2, S
 

@@ -21,6 +21,14 @@ fixes no bit stream):
 Phi^{-1} here is scipy's ``ndtri`` (a library primitive); the library builds
 its own table with its own inverse-CDF code and the tests compare the two
 tables entry by entry.
+
+The Rademacher embedding (Sec. 2 lists it beside the Gaussian one) uses one
+bit per entry:
+* entry (i, r) takes bit (r mod 128) of the Philox4x32-10 output for
+      counter = (floor(r/128) mod 2^32, floor(r/128) div 2^32, i, stream),
+  bit b being bit (b mod 32) of word floor(b/32);
+* Theta(i, r) = (1 - 2 bit) / sqrt(k): +-1/sqrt(k), so E[Theta^T Theta] = I and
+  every column of Theta has unit norm exactly.
 """
 import numpy as np
 from scipy.special import ndtri
@@ -83,3 +91,43 @@ def theta_levels(seed, k, row_offset, m, stream=0, rows=None):
 def theta(seed, k, row_offset, m, stream=0):
     """Dense Theta[:, row_offset:row_offset+m] in FP64 (for small m only)."""
     return theta_scale(k) * theta_levels(seed, k, row_offset, m, stream)
+
+
+GAUSSIAN, RADEMACHER = "gaussian", "rademacher"
+
+
+def rademacher_signs(seed, k, row_offset, m, stream=0, rows=None):
+    """The k x m array of +-1 (float64) for rows r = row_offset .. row_offset+m-1 (one bit each)."""
+    sel = np.arange(k) if rows is None else np.asarray(rows)
+    if m == 0:
+        return np.zeros((len(sel), 0))
+    q0 = row_offset // 128
+    q1 = (row_offset + m - 1) // 128
+    q = np.arange(q0, q1 + 1, dtype=np.uint64)[None, :]          # one Philox call per 128 rows
+    i = sel.astype(np.uint64)[:, None]
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    words = philox4x32_10(q & np.uint64(0xFFFFFFFF), q >> np.uint64(32),
+                          i, np.uint64(stream), seed & 0xFFFFFFFF, seed >> 32)
+    bits = np.empty((len(sel), q.shape[1], 128), dtype=np.int64)
+    for b in range(128):
+        bits[:, :, b] = ((words[b >> 5] >> np.uint64(b & 31)) & np.uint64(1)).astype(np.int64)
+    bits = bits.reshape(len(sel), -1)
+    start = row_offset - 128 * q0
+    return 1.0 - 2.0 * bits[:, start:start + m]
+
+
+def levels(seed, k, row_offset, m, stream=0, rows=None, dist=GAUSSIAN):
+    """Theta / scale(k, dist): the integer levels (Gaussian table) or the signs (Rademacher)."""
+    if dist == RADEMACHER:
+        return rademacher_signs(seed, k, row_offset, m, stream, rows)
+    return theta_levels(seed, k, row_offset, m, stream, rows)
+
+
+def scale(k, dist=GAUSSIAN):
+    """Theta = scale(k, dist) * levels(...): 1/sqrt(k v) (Gaussian table) or 1/sqrt(k)."""
+    return 1.0 / np.sqrt(float(k)) if dist == RADEMACHER else theta_scale(k)
+
+
+def dense(seed, k, row_offset, m, stream=0, dist=GAUSSIAN):
+    """Dense Theta[:, row_offset:row_offset+m] in FP64 for either distribution (small m only)."""
+    return scale(k, dist) * levels(seed, k, row_offset, m, stream, dist=dist)

@@ -57,7 +57,15 @@ struct TcCfg {
   static constexpr uint32_t P_COL = 64;
   static constexpr uint32_t L_COL = 192;
   static constexpr int X_BYTES = kTR * kTN * 4;     // the prefetched X tile (column-major)
-  static constexpr int SMEM = Q_BYTES + 3 * kRSlice + X_BYTES + 4 * 16 * 16 * 4 + 3 * 64 * 4 + 4 * 64 * 4 + 64;
+  // byte offsets of the dynamic shared memory
+  static constexpr int OFF_R = Q_BYTES;                   // 3 R pieces
+  static constexpr int OFF_X = OFF_R + 3 * kRSlice;       // X tile
+  static constexpr int OFF_RD = OFF_X + X_BYTES;          // diagonal blocks, 4 x 16 x 16 floats
+  static constexpr int OFF_DS = OFF_RD + 4 * 256 * 4;     // dinv, Sc, Isc: 3 x 64 floats
+  static constexpr int OFF_WMAX = OFF_DS + 3 * 64 * 4;    // per-warp column maxima: 4 x 64 words
+  static constexpr int OFF_SRC = OFF_WMAX + 4 * 64 * 4;   // source columns: 64 ints
+  static constexpr int SMEM = OFF_SRC + 64 * 4;
+  static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
 };
 
 struct TcTrsmArgs {
@@ -152,14 +160,14 @@ template <class TX, bool GRAM>
 __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
   using C = TcCfg<GRAM>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *Qs = smem;                                   // slice buffer, K-major core matrices
-  unsigned char *Rs = Qs + C::Q_BYTES;                        // 3 slices of R (B operands)
-  unsigned char *Xs = Rs + 3 * kRSlice;                       // the prefetched X tile
-  float *Rd = reinterpret_cast<float *>(Xs + C::X_BYTES);     // diagonal blocks, Rd[J][c][i]
-  float *Ds = Rd + 4 * 256;                                   // fl32(1 / R_jj)
-  float *Sc = Ds + 64, *Isc = Sc + 64;                        // Gram split scales per column
-  unsigned *Wmax = reinterpret_cast<unsigned *>(Isc + 64);    // per-warp column maxima (4 x 64)
-  int *Src = reinterpret_cast<int *>(Wmax + 4 * 64);          // source column of X per column
+  unsigned char *Qs = smem;                                           // slice buffer, K-major core matrices
+  unsigned char *Rs = smem + C::OFF_R;                                // 3 slices of R (B operands)
+  unsigned char *Xs = smem + C::OFF_X;                                // the prefetched X tile
+  float *Rd = reinterpret_cast<float *>(smem + C::OFF_RD);            // diagonal blocks, Rd[J][c][i]
+  float *Ds = reinterpret_cast<float *>(smem + C::OFF_DS);            // fl32(1 / R_jj)
+  float *Sc = Ds + 64, *Isc = Sc + 64;                                // Gram split scales per column
+  unsigned *Wmax = reinterpret_cast<unsigned *>(smem + C::OFF_WMAX);  // per-warp column maxima (4 x 64)
+  int *Src = reinterpret_cast<int *>(smem + C::OFF_SRC);              // source column of X per column
   __shared__ uint64_t bar_upd, bar_gram, bar_drain;
   __shared__ uint32_t tslot;
   __shared__ int s_fail;

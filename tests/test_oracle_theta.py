@@ -102,3 +102,30 @@ def test_theta_is_a_subspace_embedding(k, n):
     s = np.linalg.svd(Th @ U, compute_uv=False)
     # Gaussian-like OSE: singular values near 1 +- sqrt(n/k)
     assert s.max() < 1 + 2 * math.sqrt(n / k) and s.min() > 1 - 2 * math.sqrt(n / k)
+
+
+def test_rademacher_signs_follow_the_bit_definition():
+    # an independent per-entry recomputation: one scalar Philox call per entry, bit picked with
+    # Python integers (entry (i, r): bit r mod 128 of the call at counter (r // 128, i))
+    from oracle.philox import philox4x32_10
+    seed, k, off, m, stream = 0x1234567890ABCDEF, 5, 77, 300, 3
+    S = theta.rademacher_signs(seed, k, off, m, stream)
+    for i in (0, 4):
+        for r in (off, off + 50, off + 51, off + 299):
+            q = r // 128
+            w = philox4x32_10(np.uint64(q & 0xFFFFFFFF), np.uint64(q >> 32), np.uint64(i), np.uint64(stream),
+                              seed & 0xFFFFFFFF, seed >> 32)
+            b = r % 128
+            bit = (int(w[b // 32]) >> (b % 32)) & 1
+            assert S[i, r - off] == 1.0 - 2.0 * bit
+    # rows= selects rows, offsets shift columns consistently
+    assert np.array_equal(theta.rademacher_signs(seed, k, off, m, stream, rows=[4, 1]), S[[4, 1]])
+    assert np.array_equal(theta.rademacher_signs(seed, k, off + 10, 20, stream), S[:, 10:30])
+
+
+def test_rademacher_theta_unit_columns_and_balance():
+    Th = theta.dense(99, 64, 0, 4096, dist=theta.RADEMACHER)
+    assert np.allclose(np.sum(Th * Th, axis=0), 1.0, rtol=0, atol=1e-15)    # unit columns exactly
+    s = np.sign(Th)
+    assert abs(np.mean(s)) < 0.02                                            # +-1 balanced
+    assert abs(np.mean(s[:, :-1] * s[:, 1:])) < 0.02                         # no pairing of neighbours
