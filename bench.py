@@ -194,10 +194,26 @@ def measure_variants(rc, inputs, timed, dev, X32, ws32, Q32):
     out["rcholqr_mixed_4Mx64"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms)}
     ms = timed(lambda: rc.rcqr_reduced(X32, K, SEED_THETA), 5, 2)
     out["reduced_mixed_4Mx64"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms)}
+    # the Rademacher embedding (one Philox bit per entry): the sketch call alone and RCholeskyQR2
+    P = rc.colmajor(K, N, torch.float64, dev)
+    ms = timed(lambda: rc.rcqr_sketch(X32, K, SEED_THETA, P=P, workspace=ws32, theta=rc.THETA_RADEMACHER), 5, 2)
+    out["sketch_rademacher_4Mx64"] = {"ms": round(ms, 4), "GB/s": gbs(m * N * 4, ms)}
+    ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32,
+                                      theta=rc.THETA_RADEMACHER), 5, 2)
+    Qr, Rr, _, _, st_r = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32,
+                                        theta=rc.THETA_RADEMACHER)
+    Gr = Qr.double().t() @ Qr.double()
+    out["rcholqr2_mixed_4Mx64_rademacher"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms),
+                                              "orth_QtQ_minus_I": spectral_dev(Gr), "status": int(st_r[0])}
+    del P, Gr
     ws_rr = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.RR2, rc.F32) + 256, dtype=torch.uint8, device=dev)
     ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.RR2, tau=1e-5, Q=Q32, workspace=ws_rr), 5, 2)
     _, _, _, rank, _ = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.RR2, tau=1e-5, Q=Q32, workspace=ws_rr)
     out["rrrcholqr2_mixed_4Mx64_tau1e-5"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms), "rank": int(rank[0])}
+    # the same with the strong RRQR (Gu-Eisenstat swaps, f = 1.5)
+    ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.SRR2, tau=1e-5, Q=Q32, workspace=ws_rr), 5, 2)
+    _, _, _, rank, _ = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.SRR2, tau=1e-5, Q=Q32, workspace=ws_rr)
+    out["srrrcholqr2_mixed_4Mx64_tau1e-5"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms), "rank": int(rank[0])}
     del ws_rr
 
     # configuration 3: 16,777,216 x 128, k = 512, RCholeskyQR2 (condition 1e8 by construction)

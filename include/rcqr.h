@@ -70,6 +70,15 @@ typedef enum {
 
 typedef enum { RCQR_F64 = 0, RCQR_F32 = 1, RCQR_BF16 = 2 } rcqr_prec;
 
+/* The distribution of Theta's entries (Sec. 2: Gaussian and Rademacher embeddings).
+ * RCQR_THETA_GAUSSIAN: the 256-level quantile table described above (the default of
+ * every call without a `theta` argument).  RCQR_THETA_RADEMACHER: entry (i, r) =
+ * (1 - 2 b) / sqrt(k) with b = bit (r mod 128) of Philox4x32-10(counter =
+ * (floor(r/128) mod 2^32, floor(r/128) div 2^32, i, stream), key = (seed mod 2^32,
+ * seed div 2^32)), bit b of the 128-bit output being bit (b mod 32) of word
+ * floor(b/32): one Philox bit per entry. */
+typedef enum { RCQR_THETA_GAUSSIAN = 0, RCQR_THETA_RADEMACHER = 1 } rcqr_theta;
+
 /* Diagnostics: the bound of every device-side wait in the tensor-core
  * sketch's pipeline, in rounds of one mbarrier poll and a sleep of at most
  * 256 ns, for all later calls of this process; 0 restores the default of 2^22
@@ -110,6 +119,12 @@ rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         int64_t k, uint64_t seed, int64_t row_offset,
                         double *P, int64_t ldp, double *colnorm2,
                         void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* rcqr_sketch with the distribution of Theta chosen by `theta` (rcqr_theta). */
+rcqr_status rcqr_sketch_theta(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                              int64_t k, uint64_t seed, int theta, int64_t row_offset,
+                              double *P, int64_t ldp, double *colnorm2,
+                              void *workspace, size_t ws_bytes, cudaStream_t stream);
 
 /* rcqr_sketch without a workspace argument, for callers that cannot provide
  * device scratch memory: a plugin whose fixed argument list has no room for a
@@ -213,6 +228,13 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         void *Q, int64_t ldq, double *R, int64_t ldr,
                         int32_t *perm, int64_t *rank,
                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
+/* rcqr_factor with the distribution of Theta chosen by `theta` (rcqr_theta). */
+rcqr_status rcqr_factor_theta(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
+                              int64_t k, uint64_t seed, int theta, int variant, double tau,
+                              void *Q, int64_t ldq, double *R, int64_t ldr,
+                              int32_t *perm, int64_t *rank,
+                              void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
 /* Reduced RCholeskyQR, Alg. 5:  P = Theta X, Y = L X, [S, R] = QR(P),
  * Z = Y R^{-1}.  L: l x m double extractor (ldl >= l), or NULL for L = Theta

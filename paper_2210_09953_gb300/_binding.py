@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "librcqr.so")
 
 F64, F32, BF16 = 0, 1, 2
 DIRECT, DIRECT2, RR, RR2, SRR, SRR2 = 0, 1, 2, 3, 4, 5
+THETA_GAUSSIAN, THETA_RADEMACHER = 0, 1
 STATUS_NAMES = {0: "RCQR_OK", -1: "RCQR_EINVAL", -2: "RCQR_ENOTSPD", -3: "RCQR_ERANK0",
                 -4: "RCQR_ECUDA", -5: "RCQR_ETIMEOUT", -6: "RCQR_EWORKSPACE", -7: "RCQR_EUNSUPPORTED"}
 
@@ -35,6 +36,8 @@ _SIGS = {
     "rcqr_theta_table": (_i32, [_vp]),
     "rcqr_theta_scale": (_dbl, [_i64]),
     "rcqr_sketch": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rcqr_sketch_theta": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _i64, _vp, _i64, _vp, _vp, _sz,
+                                 _vp]),
     "rcqr_small_qr": (_i32, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rcqr_qrcp": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rcqr_srrqr": (_i32, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _vp, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
@@ -45,6 +48,8 @@ _SIGS = {
     "rcqr_chol_update": (_i32, [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
     "rcqr_factor": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _dbl, _vp, _i64, _vp, _i64,
                            _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rcqr_factor_theta": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _i32, _dbl, _vp, _i64, _vp,
+                                 _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rcqr_reduced": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _vp, _i64, _i64, _vp, _i64, _vp,
                             _i64, _vp, _i64, _vp, _sz, _vp, _vp]),
 }
@@ -126,15 +131,19 @@ def colmajor(m, n, dtype, device, ld=None):
     return torch.empty((n, ld), dtype=dtype, device=device).t()[:m, :]
 
 
-def rcqr_sketch(X, k, seed, row_offset=0, P=None, colnorm2=None, workspace=None):
+def rcqr_sketch(X, k, seed, row_offset=0, P=None, colnorm2=None, workspace=None, theta=THETA_GAUSSIAN):
     m, n = X.shape
     prec = prec_of(X.dtype)
     if P is None:
         P = colmajor(k, n, torch.float64, X.device)
     ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, DIRECT, prec), X.device)
     wp, wb = _aligned_ptr(ws)
-    _check("rcqr_sketch", lib.rcqr_sketch(_ptr(X), m, n, _ld(X), prec, k, seed, row_offset, _ptr(P), _ld(P),
-                                          _ptr(colnorm2), wp, wb, _stream()))
+    if theta == THETA_GAUSSIAN:
+        _check("rcqr_sketch", lib.rcqr_sketch(_ptr(X), m, n, _ld(X), prec, k, seed, row_offset, _ptr(P), _ld(P),
+                                              _ptr(colnorm2), wp, wb, _stream()))
+    else:
+        _check("rcqr_sketch_theta", lib.rcqr_sketch_theta(_ptr(X), m, n, _ld(X), prec, k, seed, theta, row_offset,
+                                                          _ptr(P), _ld(P), _ptr(colnorm2), wp, wb, _stream()))
     return P
 
 
@@ -224,7 +233,8 @@ def rcqr_chol_update(A, R, rank=None):
     return Rp, status
 
 
-def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=None, rank=None, status=None):
+def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=None, rank=None, status=None,
+                theta=THETA_GAUSSIAN):
     """Returns (Q, R, perm, rank, status); perm is None for the direct variants.  Q, R, rank and
     status may be given (preallocated buffers); the others are allocated on the current stream."""
     m, n = X.shape
@@ -241,9 +251,14 @@ def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=
         status = torch.zeros(2, dtype=torch.int32, device=dev)
     ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, variant, prec), dev)
     wp, wb = _aligned_ptr(ws)
-    _check("rcqr_factor", lib.rcqr_factor(_ptr(X), m, n, _ld(X), prec, k, seed, variant, float(tau), _ptr(Q),
-                                          _ld(Q), _ptr(R), _ld(R), _ptr(perm), _ptr(rank), wp, wb, _ptr(status),
-                                          _stream()))
+    if theta == THETA_GAUSSIAN:
+        _check("rcqr_factor", lib.rcqr_factor(_ptr(X), m, n, _ld(X), prec, k, seed, variant, float(tau), _ptr(Q),
+                                              _ld(Q), _ptr(R), _ld(R), _ptr(perm), _ptr(rank), wp, wb, _ptr(status),
+                                              _stream()))
+    else:
+        _check("rcqr_factor_theta", lib.rcqr_factor_theta(_ptr(X), m, n, _ld(X), prec, k, seed, theta, variant,
+                                                          float(tau), _ptr(Q), _ld(Q), _ptr(R), _ld(R), _ptr(perm),
+                                                          _ptr(rank), wp, wb, _ptr(status), _stream()))
     return Q, R, perm, rank, status
 
 

@@ -42,6 +42,8 @@ namespace {
 
 bool valid_prec(int prec) { return prec == RCQR_F64 || prec == RCQR_F32 || prec == RCQR_BF16; }
 
+bool valid_theta(int theta) { return theta == RCQR_THETA_GAUSSIAN || theta == RCQR_THETA_RADEMACHER; }
+
 bool valid_sizes(int64_t m, int64_t n, int64_t k) {
   return m >= 1 && n >= 1 && n <= 256 && k >= n && k <= 2048 && (k % 8) == 0;
 }
@@ -121,17 +123,24 @@ size_t rcqr_workspace_size(int64_t m, int64_t n, int64_t k, int variant, int pre
   return ((fixed + 255) & ~size_t(255)) + extra + 512;
 }
 
-rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
-                        uint64_t seed, int64_t row_offset, double *P, int64_t ldp,
-                        double *colnorm2, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+rcqr_status rcqr_sketch_theta(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                              uint64_t seed, int theta, int64_t row_offset, double *P, int64_t ldp,
+                              double *colnorm2, void *workspace, size_t ws_bytes, cudaStream_t stream) {
   if (!X || !P || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m || ldp < k ||
-      row_offset < 0)
+      row_offset < 0 || !valid_theta(theta))
     return RCQR_EINVAL;
   if (!workspace || !aligned(workspace) || ws_bytes < sketch_workspace(m, n, k, row_offset, prec))
     return RCQR_EWORKSPACE;
   Workspace w(workspace, ws_bytes);
   return cuda_status(
-      launch_sketch(X, m, n, ldx, prec, k, seed, 0, row_offset, P, ldp, colnorm2, w, stream));
+      launch_sketch(X, m, n, ldx, prec, k, seed, 0, row_offset, P, ldp, colnorm2, w, stream, nullptr, theta));
+}
+
+rcqr_status rcqr_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                        uint64_t seed, int64_t row_offset, double *P, int64_t ldp,
+                        double *colnorm2, void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  return rcqr_sketch_theta(X, m, n, ldx, prec, k, seed, RCQR_THETA_GAUSSIAN, row_offset, P, ldp, colnorm2,
+                           workspace, ws_bytes, stream);
 }
 
 rcqr_status rcqr_small_qr(const double *P, int64_t k, int64_t n, int64_t ldp, double *S,
@@ -236,6 +245,15 @@ rcqr_status rcqr_factor(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                            workspace, ws_bytes, dev_status, stream);
 }
 
+rcqr_status rcqr_factor_theta(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                              uint64_t seed, int theta, int variant, double tau, void *Q, int64_t ldq,
+                              double *R, int64_t ldr, int32_t *perm, int64_t *rank, void *workspace,
+                              size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+  if (!valid_theta(theta)) return RCQR_EINVAL;
+  return rcqr::factor_impl(X, m, n, ldx, prec, k, seed, 0u, variant, tau, Q, ldq, R, ldr, perm, rank,
+                           workspace, ws_bytes, dev_status, stream, theta);
+}
+
 }  // extern "C"
 
 namespace rcqr {
@@ -245,7 +263,7 @@ namespace rcqr {
 rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                         uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
-                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream) {
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream, int dist) {
   if (!X || !Q || !R || !dev_status || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m ||
       ldq < m || ldr < n || variant < 0 || variant > 5)
     return RCQR_EINVAL;
@@ -278,7 +296,7 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
   RCQR_TRY(launch_reset_status(dev_status, stream));
   // Alg. 2 / Alg. 7 step 1 (with D of Sec. 4 in the same pass for RR)
   RCQR_TRY(launch_sketch(X, m, n, ldx, prec, k, seed, stream_id, 0, b.P, k, rr ? b.colnorm2 : nullptr,
-                         *scratch(), stream, dev_status));
+                         *scratch(), stream, dev_status, dist));
   const int32_t *pm = nullptr;
   const int64_t *rkp = nullptr;
   if (!rr) {

@@ -55,7 +55,8 @@ inline cudaError_t set_smem(K *kernel, int bytes) {
 rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                         uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
-                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream,
+                        int dist = RCQR_THETA_GAUSSIAN);
 
 // f of the strong rank-revealing QR in the RCQR_SRR / RCQR_SRR2 variants (Sec. 4, Sec. 6.1).
 constexpr double kStrongRrqrF = 1.5;
@@ -72,13 +73,14 @@ size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int
 cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                           uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                           int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st,
-                          int *dev_status = nullptr);
+                          int *dev_status = nullptr, int dist = RCQR_THETA_GAUSSIAN);
 // The exact tensor-core sketch (tcgen05): partial sums per CTA in the workspace;
 // colnorm2 (nullable) receives the squared column norms from the same pass.
 size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec);
 cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                              uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
-                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st);
+                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st,
+                             int dist = RCQR_THETA_GAUSSIAN);
 // The same sketch with its partial sums in a caller-given device buffer of
 // scratch_doubles doubles (fewer row groups when the buffer is small); no workspace.
 cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,

@@ -230,9 +230,9 @@ size_t sketch_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, int
 cudaError_t launch_sketch(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                           uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
                           int64_t ldp, double *colnorm2, Workspace &ws, cudaStream_t st,
-                          int *dev_status) {
+                          int *dev_status, int dist) {
   return launch_sketch_tc(X, m, n, ldx, prec, k, seed, stream_id, row_offset, P, ldp, colnorm2, dev_status, ws,
-                          st);
+                          st, dist);
 }
 
 cudaError_t launch_sketch_into(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,

@@ -42,6 +42,7 @@
 // RCQR_ETIMEOUT in the status word.
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 
 #include "common.cuh"
 #include "rcqr_internal.h"
@@ -113,6 +114,7 @@ struct TcArgs {
   int *status;        // nullable
   uint32_t polls;     // bound of every pipeline wait (rounds of poll + sleep)
   ThetaTable theta;   // the 256 levels T[t], passed by value (no device state to set up)
+  int dist;           // RCQR_THETA_GAUSSIAN (levels from Philox bytes) or RCQR_THETA_RADEMACHER (bits)
 };
 
 constexpr int EMPTY_EXP = -0x40000000;
@@ -331,6 +333,46 @@ struct ThetaCalls {
       unsigned char *dst = sA + off[u];
       *reinterpret_cast<uint4 *>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       *reinterpret_cast<uint4 *>(dst + 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+  }
+};
+
+// The Rademacher Theta tile of one stage: thread tt (< KCH * 128) owns Theta row
+// il = tt % 128 of chunk c = tt / 128 (row i = (kgi KCH + c) 128 + il).  Its 32 entries of
+// the stage at global X rows r0 .. r0+31 are bits (r0 mod 128) .. +31 of the Philox call at
+// counter (r0 / 128, i): one call per four stages, kept in registers; bit 0 -> +1, 1 -> -1.
+template <int KCH>
+struct RadCalls {
+  uint32_t row;     // Theta row i (>= k: a zero row)
+  uint32_t off;     // byte offset of the row's first 16 bytes in the tile
+  uint4 w;
+
+  __device__ __forceinline__ void init(int tt, int kgi) {
+    const int c = tt >> 7, il = tt & 127;
+    row = (uint32_t)((kgi * KCH + c) * 128 + il);
+    off = (uint32_t)(c * (128 * kBK * 2) + (il >> 3) * (kBK * 16) + (il & 7) * 16);
+    w = make_uint4(0u, 0u, 0u, 0u);
+  }
+
+  __device__ __forceinline__ void tile(unsigned char *sA, int64_t r0, const TcArgs &a) {
+    const int sub = (int)((r0 >> 5) & 3);          // the call's 32-bit word for these 32 rows
+    if (sub == 0) {                                // stages start on 128-row boundaries at sub 0
+      const uint64_t q = (uint64_t)(r0 >> 7);
+      w = row < (uint32_t)a.k ? philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), row, a.stream_id), a.rk)
+                              : make_uint4(0u, 0u, 0u, 0u);
+    }
+    const uint32_t word = sub == 0 ? w.x : (sub == 1 ? w.y : (sub == 2 ? w.z : w.w));
+    const bool live = row < (uint32_t)a.k;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      uint32_t pv[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const uint32_t t = word >> (8 * kc + 2 * p);
+        // bf16 +-1 pair: sign bits 15 and 31 from bits 0 and 1 of t
+        pv[p] = live ? (0x3F803F80u | ((t << 15) & 0x8000u) | ((t << 30) & 0x80000000u)) : 0u;
+      }
+      *reinterpret_cast<uint4 *>(sA + off + kc * 128) = make_uint4(pv[0], pv[1], pv[2], pv[3]);
     }
   }
 };
@@ -598,12 +640,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     // ---- Theta producers
     const uint32_t *tabp = table + lane;
     ThetaCalls<KCH, NTW> calls;
-    calls.init(tid, kgi);
+    RadCalls<KCH> rad;
+    const bool rademacher = a.dist == RCQR_THETA_RADEMACHER;
+    if (rademacher) rad.init(tid, kgi);
+    else calls.init(tid, kgi);
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
       const int b = it / kSPB, st = it % kSPB;
-      calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, (bb + b) * kBlockRows + st * kBK, a);
+      const int64_t r0 = (bb + b) * kBlockRows + st * kBK;
+      if (rademacher) rad.tile(stage_base + slot * K::STAGE_BYTES, r0, a);
+      else calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, r0, a);
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
@@ -855,7 +902,8 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int64_t k, int64_t row_offset, 
 
 cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                              uint64_t seed, uint32_t stream_id, int64_t row_offset, double *P,
-                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st) {
+                             int64_t ldp, double *colnorm2, int *dev_status, Workspace &ws, cudaStream_t st,
+                             int dist) {
   const TcPlan p = plan_tc(m, n, k, row_offset, prec);
   double *partial = ws.take<double>((size_t)p.groups * n * k);
   long long *acc64 = ws.take<long long>(acc64_count(p));
@@ -888,6 +936,7 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
   a.status = dev_status;
   a.polls = wait_polls();
   a.theta = theta_table();
+  a.dist = dist;
   dim3 grid((unsigned)(p.kgrp * p.ngrp), (unsigned)p.groups);
   cudaError_t e;
   {
@@ -914,8 +963,9 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
     default: e = launch_tc_prec<RCQR_BF16>(a, p, grid, st);
   }
   if (e != cudaSuccess) return e;
+  const double c = dist == RCQR_THETA_RADEMACHER ? 1.0 / std::sqrt((double)k) : theta_scale(k);
   sketch_tc_reduce_kernel<<<(unsigned)((k * n * 32 + 255) / 256), 256, 0, st>>>(partial, p.groups, (int)k, (int)n,
-                                                                          theta_scale(k), P, ldp);
+                                                                          c, P, ldp);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,95 @@
+"""GPU parity of the sketch with the Rademacher embedding (one Philox bit per entry, Sec. 2)
+against the oracle (oracle.theta.rademacher_signs, oracle.rcqr.sketch(dist="rademacher")).
+
+* Integer X: bit-exact (every partial sum is an integer below 2^53).
+* Other X: column-wise relative SKETCH_TOL, the tolerance of the Gaussian sketch (the same
+  exact digit slices; the +-1 levels only shrink the products).
+* Row shards at offsets that are not multiples of the 128-row Philox block add up to the
+  whole; RCholeskyQR2 driven by it matches the oracle run with the same embedding.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rcqr as orc
+from oracle import theta as oth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+SKETCH_TOL = {"f64": 1e-12, "f32": 1e-11, "bf16": 1e-6}
+RAD = oth.RADEMACHER
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2210_09953_gb300 import _binding
+    return _binding
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    from paper_2210_09953_gb300 import inputs as inp
+    return inp
+
+
+def host64(t):
+    return t.detach().to("cpu", torch.float64).numpy()
+
+
+def colrel(A, B):
+    den = np.linalg.norm(B, axis=0)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.linalg.norm(A - B, axis=0) / den))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("off", [0, 77])
+def test_rademacher_sketch_integer_input_is_bit_exact(rc, inputs, prec, off):
+    m, n, k = 40021, 19, 64
+    X = inputs.integer_matrix(m, n, 6, dtype=prec, device=DEV)
+    P = rc.rcqr_sketch(X, k, 0xBEEF, row_offset=off, theta=rc.THETA_RADEMACHER)
+    torch.cuda.synchronize()
+    Po = orc.sketch(host64(X), k, 0xBEEF, row_offset=off, dist=RAD)
+    assert np.array_equal(host64(P), Po)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m,n,k", [(1000, 1, 8), (20000, 64, 256), (3001, 130, 264)])
+def test_rademacher_sketch_parity(rc, inputs, prec, m, n, k):
+    X = inputs.svd_matrix(m, n, 1e6, 31 + m, dtype=prec, device=DEV)
+    P = rc.rcqr_sketch(X, k, 0xCAFE + n, theta=rc.THETA_RADEMACHER)
+    torch.cuda.synchronize()
+    Po = orc.sketch(host64(X), k, 0xCAFE + n, dist=RAD)
+    assert colrel(host64(P), Po) <= SKETCH_TOL[prec]
+
+
+def test_rademacher_sketch_shards_add_up(rc, inputs):
+    m, n, k, a = 30000, 16, 64, 12345
+    X = inputs.svd_matrix(m, n, 1e3, 3, dtype="f64", device=DEV)
+    P = host64(rc.rcqr_sketch(X, k, 42, theta=rc.THETA_RADEMACHER))
+    P1 = host64(rc.rcqr_sketch(X[:a], k, 42, row_offset=0, theta=rc.THETA_RADEMACHER))
+    P2 = host64(rc.rcqr_sketch(X[a:], k, 42, row_offset=a, theta=rc.THETA_RADEMACHER))
+    assert colrel(P1 + P2, P) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rcholqr2_with_rademacher_theta(rc, inputs, prec):
+    m, n, k, cond = 20011, 64, 256, 1e6
+    X = inputs.svd_matrix(m, n, cond, 1201, dtype=prec, device=DEV)
+    Q, R, _, _, status = rc.rcqr_factor(X, k, 77, variant=rc.DIRECT2, theta=rc.THETA_RADEMACHER)
+    torch.cuda.synchronize()
+    assert int(status[0]) == 0
+    Xh = host64(X)
+    Qo, Ro, _ = orc.rcholqr2(Xh, k, 77, dist=RAD)
+    Qg, Rg = host64(Q), host64(R)
+    ub = U if prec == "f64" else 2.0 ** -24
+    assert np.linalg.norm(Qg @ Rg - Xh) / np.linalg.norm(Xh) <= max(1e-12, 10 * n * ub)
+    assert orc.orthogonality(Qg) <= (max(1e-12, 100 * n * ub) if prec == "f64" else 1e-6)
+    if prec == "f64":
+        kap = orc.condition_number(Xh)
+        assert colrel(Rg, Ro) <= max(1e-12, 10 * n * U * kap)

@@ -94,14 +94,22 @@ def test_factor_strong_rank_revealing(rc, inputs, prec, variant):
         Qo, Ro, permo, ro = orc.rrrcholqr2(Xh, k, seed, tau, strong_f=F)
     assert int(status[0]) == 0
     assert int(rank[0]) == ro == r
-    assert perm.cpu().numpy().tolist() == permo.tolist()
+    # the kept columns are unique; the order of the discarded ones is decided by noise-level
+    # norms (near-ties), so only their set is compared
+    pg = perm.cpu().numpy()
+    assert pg[:r].tolist() == permo[:r].tolist()
+    assert sorted(pg[r:].tolist()) == sorted(permo[r:].tolist())
     Qg, Rg = host64(Q), host64(R)
     assert np.all(Qg[:, r:] == 0) and np.all(Rg[r:] == 0)
     uq = 2.0 ** -53 if prec == "f64" else 2.0 ** -24
     D = np.linalg.norm(Xh, axis=0)
-    E = (Xh[:, permo] - Qg[:, :r] @ Rg[:r]) / D[permo][None, :]
+    E = (Xh[:, pg] - Qg[:, :r] @ Rg[:r]) / D[pg][None, :]
     assert np.linalg.norm(E) <= 2 * tau + 100 * uq
-    assert colrel(Qg[:, :r] @ Rg[:r], Qo @ Ro) <= max(1e-10, 100 * uq)
+    # Q R in the original column order against the oracle's
+    Yg, Yo = np.zeros_like(Xh), np.zeros_like(Xh)
+    Yg[:, pg] = Qg[:, :r] @ Rg[:r]
+    Yo[:, permo] = Qo @ Ro
+    assert colrel(Yg, Yo) <= max(1e-10, 100 * uq)
     if variant == 5:
         assert orc.orthogonality(Qg[:, :r]) <= max(1e-12, 100 * r * uq)
 

@@ -222,3 +222,23 @@ def test_rcholqr_f32_well_conditioned_q():
     assert eps < 1
     assert (1 + eps) ** -0.5 - slack <= s.min() and s.max() <= (1 - eps) ** -0.5 + slack
     assert np.linalg.norm(S - Th @ Q.astype(np.float64)) <= 6.1 * 2.0 ** -24 * n ** 1.5 * kappa
+
+
+def test_rademacher_sketch_exact_on_integers_bruteforce():
+    rng = np.random.default_rng(19)
+    m, n, k, seed, off = 333, 3, 24, 4321, 90
+    X = rng.integers(-128, 128, size=(m, n))
+    Sg = theta.rademacher_signs(seed, k, off, m).astype(np.int64)
+    exact = [[sum(int(Sg[i, r]) * int(X[r, j]) for r in range(m)) for j in range(n)] for i in range(k)]
+    P = rcqr.sketch(X.astype(np.float64), k, seed, row_offset=off, dist=theta.RADEMACHER)
+    assert np.array_equal(P, (1.0 / np.sqrt(k)) * np.array(exact, dtype=np.float64))
+
+
+def test_rcholqr2_with_rademacher_theta():
+    # a Rademacher embedding serves Alg. 3 like the Gaussian one: R equals Householder R of X
+    m, n, k, kappa = 3000, 10, 80, 1e6
+    X, _ = svd_matrix(m, n, kappa, 23)
+    Q, R, _ = rcqr.rcholqr2(X, k, 8, dist=theta.RADEMACHER)
+    _, Rh = linalg.householder_qr(X)
+    assert rcqr.orthogonality(Q) <= 100 * n * U64
+    assert np.max(np.abs(R - Rh) / np.abs(Rh).max(axis=0)[None, :]) <= 10 * n * U64 * kappa
