@@ -467,6 +467,19 @@ def run_ours(args):
                     "h2d_and_d2h_together_ms": round(ms_both, 3),
                     "steps": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in t.items()} for t in tl]}
 
+    # measured arithmetic roofs (throughput probes, each launch timed alone)
+    scratch = torch.empty(int(rc.lib.rcqr_probe_scratch_bytes()), dtype=torch.uint8, device=dev)
+    probes = {}
+    for name, kind, iters in (("philox_calls", rc.PROBE_PHILOX, 2000), ("ffma", rc.PROBE_FFMA, 20000),
+                              ("dfma", rc.PROBE_DFMA, 2000), ("imad", rc.PROBE_IMAD, 20000)):
+        ops = [0]
+
+        def run_probe(kind=kind, iters=iters):
+            ops[0] = rc.rcqr_probe(kind, iters, scratch)
+        ms = timed(run_probe, 3, 1)
+        probes[name] = ops[0] / (ms * 1e-3)
+    del scratch
+
     variants = None
     if not args.no_variants and m == M:
         variants = measure_variants(rc, inputs, timed, dev, X32, ws32, Q32)
@@ -497,6 +510,13 @@ def run_ours(args):
                      m * N * 8, ms_trsm),
     }
     dominant = max(roofs, key=lambda k_: roofs[k_]["ms"])
+    # the sketch against its generation roof: k Theta entries per X row, 16 entries per
+    # Philox call for the Gaussian levels (measured Philox calls/s x 16 entries/call)
+    gen_peak = probes["philox_calls"] * 16 / 1e9
+    gen_ach = K * m / (ms_sketch * 1e-3) / 1e9
+    roof_gen = {"kernel": roofs["sketch"]["kernel"], "bound": "alu", "achieved": round(gen_ach, 2),
+                "peak": round(gen_peak, 2), "unit": "G Theta entries/s", "frac": round(gen_ach / gen_peak, 4),
+                "peak_source": "measured: rcqr_probe Philox4x32-10 calls/s x 16 bytes (entries) per call"}
     # per factorization (mixed path, Alg. 3): status reset, sketch (block exponents, tensor-core
     # sketch, reduction), Householder R + sign fix, rank, substitution prep + substitution fused
     # with the Gram + Gram reduction, Cholesky update, substitution prep + substitution
@@ -521,6 +541,10 @@ def run_ours(args):
             "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4), "trsm_gram": round(ms_tg, 4)},
             "roofline": roofs[dominant],
             "rooflines": roofs,
+            "roofline_sketch_generation": roof_gen,
+            "measured_rates": {"philox_calls_per_s": round(probes["philox_calls"], 1),
+                               "fp32_fma_per_s": round(probes["ffma"], 1), "fp64_fma_per_s": round(probes["dfma"], 1),
+                               "int32_mad_per_s": round(probes["imad"], 1)},
             "clocks": clocks,
             "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8,

@@ -89,6 +89,17 @@ typedef enum { RCQR_THETA_GAUSSIAN = 0, RCQR_THETA_RADEMACHER = 1 } rcqr_theta;
  * not stream-ordered: change it only while no sketch is queued. */
 uint32_t rcqr_set_wait_polls(uint32_t polls);
 
+/* Diagnostics (the paper has no counterpart): throughput probes for the rooflines of
+ * arithmetic-bound kernels.  rcqr_probe launches, on `stream`, one kernel of 4 CTAs of
+ * 256 threads per SM that runs `iters` iterations of independent chains of one
+ * operation kind and writes one checksum per thread to `scratch` (device, at least
+ * rcqr_probe_scratch_bytes() bytes).  It returns the number of operations the kernel
+ * performs (Philox4x32-10 calls, FP32 FMAs, FP64 FMAs or 32-bit integer multiply-adds),
+ * or -1 on a bad argument or launch error; time the call with CUDA events on `stream`. */
+typedef enum { RCQR_PROBE_PHILOX = 0, RCQR_PROBE_FFMA = 1, RCQR_PROBE_DFMA = 2, RCQR_PROBE_IMAD = 3 } rcqr_probe_kind;
+size_t rcqr_probe_scratch_bytes(void);
+int64_t rcqr_probe(int kind, int iters, void *scratch, size_t scratch_bytes, cudaStream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *rcqr_status_string(int status);
 

@@ -33,6 +33,8 @@ _SIGS = {
     "rcqr_workspace_size": (_sz, [_i64, _i64, _i64, _i32, _i32]),
     "rcqr_reduced_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i32]),
     "rcqr_set_wait_polls": (ctypes.c_uint32, [ctypes.c_uint32]),
+    "rcqr_probe_scratch_bytes": (_sz, []),
+    "rcqr_probe": (_i64, [_i32, _i32, _vp, _sz, _vp]),
     "rcqr_theta_table": (_i32, [_vp]),
     "rcqr_theta_scale": (_dbl, [_i64]),
     "rcqr_sketch": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
@@ -114,6 +116,17 @@ def rcqr_reduced_workspace_size(m, n, k, l=0, prec=F64):
 def rcqr_set_wait_polls(polls):
     """Bound of the sketch pipeline's device waits for later calls (0: the default); returns the previous one."""
     return int(lib.rcqr_set_wait_polls(polls))
+
+
+PROBE_PHILOX, PROBE_FFMA, PROBE_DFMA, PROBE_IMAD = 0, 1, 2, 3
+
+
+def rcqr_probe(kind, iters, scratch):
+    """Launch one throughput probe on the current stream; returns its operation count."""
+    ops = int(lib.rcqr_probe(kind, iters, _ptr(scratch), scratch.numel() * scratch.element_size(), _stream()))
+    if ops < 0:
+        raise RcqrError("rcqr_probe", -1)
+    return ops
 
 
 def rcqr_theta_table():

@@ -3,8 +3,8 @@
 // the second pass (Alg. 3 step 2).
 //
 // A CTA of 128 threads takes tiles of 128 rows (thread t owns row t of the tile
-// and TMEM lane t); the next tile's X is copied into shared memory (cp.async)
-// while the current one is processed.  The 64 (padded) columns form four blocks
+// and TMEM lane t; two or three CTAs per SM hide each other's latencies).  The
+// 64 (padded) columns form four blocks
 // of 16.  For block J the thread forms y_J = x_J - (sum_{I<J} q_I R_{I,J}) and
 // solves the 16 x 16 triangular system y_J = q_J R_{J,J} by substitution in
 // FP32 registers (the diagonal block is never inverted).  The off-diagonal
@@ -56,16 +56,15 @@ struct TcCfg {
   static constexpr uint32_t NCOLS = GRAM ? 256u : 64u;   // TMEM: update acc (48) [+ P 128 + L 64]
   static constexpr uint32_t P_COL = 64;
   static constexpr uint32_t L_COL = 192;
-  static constexpr int X_BYTES = kTR * kTN * 4;     // the prefetched X tile (column-major)
   // byte offsets of the dynamic shared memory
   static constexpr int OFF_R = Q_BYTES;                   // 3 R pieces
-  static constexpr int OFF_X = OFF_R + 3 * kRSlice;       // X tile
-  static constexpr int OFF_RD = OFF_X + X_BYTES;          // diagonal blocks, 4 x 16 x 16 floats
+  static constexpr int OFF_RD = OFF_R + 3 * kRSlice;      // diagonal blocks, 4 x 16 x 16 floats
   static constexpr int OFF_DS = OFF_RD + 4 * 256 * 4;     // dinv, Sc, Isc: 3 x 64 floats
   static constexpr int OFF_WMAX = OFF_DS + 3 * 64 * 4;    // per-warp column maxima: 4 x 64 words
   static constexpr int OFF_SRC = OFF_WMAX + 4 * 64 * 4;   // source columns: 64 ints
   static constexpr int SMEM = OFF_SRC + 64 * 4;
-  static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
+  static constexpr int CTAS = GRAM ? 2 : 3;               // per SM (TMEM, registers, shared memory)
+  static_assert(CTAS * (SMEM + 2048) <= 228 * 1024, "CTAS CTAs per SM");
 };
 
 struct TcTrsmArgs {
@@ -81,7 +80,6 @@ struct TcTrsmArgs {
   int64_t ldq;
   double *partial;      // GRAM: one n x n FP64 partial per CTA
   int *status;          // nullable: RCQR_ETIMEOUT on a wait that gave up
-  int vec;              // X's columns start on 16-byte boundaries at every tile: cp.async prefetch
 };
 
 __device__ __forceinline__ float to_f32v(float x) { return x; }
@@ -131,38 +129,12 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, int *fa
   return false;
 }
 
-__device__ __forceinline__ void cp_async16_zf(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(src_bytes)
-               : "memory");
-}
-
-// Starts the copy of tile `tile`'s X rows (columns Src[c]; -1: zeros) into Xs, column-major
-// (column c at Xs + c * 128 elements); rows beyond m are zero-filled.
-template <class TX>
-__device__ __forceinline__ void prefetch_x(const TX *X, int64_t m, int64_t ldx, int64_t tile, const int *Src,
-                                           unsigned char *Xs) {
-  constexpr int EPC = 16 / (int)sizeof(TX);          // elements per 16-byte chunk
-  constexpr int CPC = kTR / EPC;                     // chunks per column
-  const int64_t row0 = tile * kTR;
-  for (int ch = threadIdx.x; ch < kTN * CPC; ch += kTR) {
-    const int c = ch / CPC, part = ch % CPC;
-    const int src = Src[c];
-    const int64_t r = row0 + (int64_t)part * EPC;
-    const int64_t left = m - r;
-    const int valid = (src >= 0 && left > 0) ? (int)(left < EPC ? left : EPC) : 0;
-    const TX *g = valid > 0 ? X + r + (int64_t)src * ldx : X;
-    cp_async16_zf(Xs + ((size_t)c * kTR + (size_t)part * EPC) * sizeof(TX), g, valid * (int)sizeof(TX));
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
 template <class TX, bool GRAM>
-__global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
+__global__ void __launch_bounds__(kTR, TcCfg<GRAM>::CTAS) trsm_tc_kernel(TcTrsmArgs a) {
   using C = TcCfg<GRAM>;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *Qs = smem;                                           // slice buffer, K-major core matrices
   unsigned char *Rs = smem + C::OFF_R;                                // 3 slices of R (B operands)
-  unsigned char *Xs = smem + C::OFF_X;                                // the prefetched X tile
   float *Rd = reinterpret_cast<float *>(smem + C::OFF_RD);            // diagonal blocks, Rd[J][c][i]
   float *Ds = reinterpret_cast<float *>(smem + C::OFF_DS);            // fl32(1 / R_jj)
   float *Sc = Ds + 64, *Isc = Sc + 64;                                // Gram split scales per column
@@ -218,7 +190,6 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
   bool gram_pending = false;
   const int64_t tiles = (a.m + kTR - 1) / kTR;
   const uint32_t row_sw = (uint32_t)(tid / 8) * C::QSBO + (uint32_t)(tid % 8) * 16;   // this row's core offset
-  if (a.vec && (int64_t)blockIdx.x < tiles) prefetch_x<TX>(X, a.m, a.ldx, blockIdx.x, Src, Xs);
 
   // folds the finished Gram MMAs of the previous tile (TMEM P region) into the Kahan sums
   auto fold = [&]() {
@@ -252,18 +223,10 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
       gram_pending = false;
     }
     float q[kTN];
-    if (a.vec) {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncthreads();
-      const TX *xs = reinterpret_cast<const TX *>(Xs);
 #pragma unroll
-      for (int j = 0; j < kTN; ++j) q[j] = to_f32v(xs[j * kTR + tid]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < kTN; ++j) {
-        const int src = Src[j];
-        q[j] = (live && src >= 0) ? to_f32v(X[row + (int64_t)src * a.ldx]) : 0.0f;
-      }
+    for (int j = 0; j < kTN; ++j) {
+      const int src = Src[j];
+      q[j] = (live && src >= 0) ? to_f32v(X[row + (int64_t)src * a.ldx]) : 0.0f;
     }
 #pragma unroll
     for (int J = 0; J < 4; ++J) {
@@ -278,14 +241,33 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) q[16 * J + c] -= __uint_as_float(v[c]);
       }
-      // substitution against the diagonal block R_{J,J}
-      const float *rd = Rd + 256 * J;
+      // substitution against the diagonal block R_{J,J}: column c of the block is 16 floats
+      // at rd + 16 c (read as float4), each dot product in two interleaved FMA chains
+      const float4 *rd4 = reinterpret_cast<const float4 *>(Rd + 256 * J);
+      const float4 *ds4 = reinterpret_cast<const float4 *>(Ds + 16 * J);
+      float dj[16];
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const float4 d = ds4[c4];
+        dj[4 * c4] = d.x; dj[4 * c4 + 1] = d.y; dj[4 * c4 + 2] = d.z; dj[4 * c4 + 3] = d.w;
+      }
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        float s = q[16 * J + c];
+        float s0 = q[16 * J + c], s1 = 0.0f;
 #pragma unroll
-        for (int i = 0; i < c; ++i) s = fmaf(-q[16 * J + i], rd[16 * c + i], s);
-        q[16 * J + c] = s * Ds[16 * J + c];
+        for (int i4 = 0; i4 < (c + 3) / 4; ++i4) {
+          const float4 rv = rd4[4 * c + i4];
+          const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = 4 * i4 + u;
+            if (i < c) {
+              if (u & 1) s1 = fmaf(-q[16 * J + i], rr[u], s1);
+              else s0 = fmaf(-q[16 * J + i], rr[u], s0);
+            }
+          }
+        }
+        q[16 * J + c] = (s0 + s1) * dj[c];
       }
       if (J < 3) {
         // the exact three-way split of q_J into the slice buffer (two 16-byte chunks per piece)
@@ -302,8 +284,6 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
         umma::fence_proxy_async();
         umma::fence_before_sync();
         __syncthreads();
-        if (J == 0 && a.vec && tile + gridDim.x < tiles)   // Xs has been read by every thread
-          prefetch_x<TX>(X, a.m, a.ldx, tile + gridDim.x, Src, Xs);
         if (tid == 0 && !*(volatile int *)&s_fail) {
           umma::fence_after_sync();
           const int N = 16 * (3 - J);
@@ -349,10 +329,14 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
 #pragma unroll
       for (int c8 = 0; c8 < kTN / 8; ++c8) {
         uint32_t hw[4], mw[4], lw[4];
+        const float4 sa = reinterpret_cast<const float4 *>(Sc)[2 * c8], sb = reinterpret_cast<const float4 *>(Sc)[2 * c8 + 1];
+        const float4 ia = reinterpret_cast<const float4 *>(Isc)[2 * c8], ib = reinterpret_cast<const float4 *>(Isc)[2 * c8 + 1];
+        const float sc8[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+        const float is8[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const int j = 8 * c8 + 2 * p;
-          split_fixed(q[j], q[j + 1], Sc[j], Sc[j + 1], Isc[j], Isc[j + 1], hw[p], mw[p], lw[p]);
+          split_fixed(q[j], q[j + 1], sc8[2 * p], sc8[2 * p + 1], is8[2 * p], is8[2 * p + 1], hw[p], mw[p], lw[p]);
         }
         const uint32_t col = 8 * c8;
         *reinterpret_cast<uint4 *>(Qs + row_sw + ((0 * C::CW + col) / 8) * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -428,8 +412,6 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
       pb[e] = failed ? nan : ((ii <= jj) ? F[ii * 64 + jj] : 0.0);
     }
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-
   // drain: every MMA issued by thread 0 has finished before TMEM is released
   if (tid == 0) {
     umma::mma_commit(&bar_drain);
@@ -445,8 +427,7 @@ __global__ void __launch_bounds__(kTR, 2) trsm_tc_kernel(TcTrsmArgs a) {
 template <bool GRAM>
 int tc_grid(int64_t m) {
   const int64_t tiles = (m + kTR - 1) / kTR;
-  // two CTAs per SM (shared memory: slice buffer, R pieces and the X tile)
-  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)2 * num_sms()));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)TcCfg<GRAM>::CTAS * num_sms()));
 }
 
 template <class TX, bool GRAM>
@@ -467,10 +448,7 @@ int trsm_tc_gram_groups(int64_t m) { return tc_grid<true>(m); }
 cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
                            const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
                            double *partial, int *status, cudaStream_t st) {
-  const size_t es = prec == RCQR_BF16 ? 2 : 4;
-  // every 16-byte chunk of a tile column starts on a 16-byte boundary
-  const int vec = ((uintptr_t)X % 16 == 0) && ((size_t)ldx * es) % 16 == 0;
-  TcTrsmArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial, status, vec};
+  TcTrsmArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial, status};
   const bool gram = partial != nullptr;
   if (gram) {
     const int grid = tc_grid<true>(m);
