@@ -247,6 +247,51 @@ rcqr_status rcqr_factor_theta(const void *X, int64_t m, int64_t n, int64_t ldx, 
                               int32_t *perm, int64_t *rank,
                               void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
 
+/* RCholeskyQR2 with an implicit Q factor (the remark after Alg. 3): Alg. 3 steps 1-3
+ * only.  Q1 (m x n, Q's type by prec) receives the Q of Alg. 2, R the final R = R' R1,
+ * Rp (n x n double, upper, diag > 0) the Cholesky factor R' of Q1^T Q1; the orthonormal
+ * factor Q = Q1 R'^{-1} is never formed (one pass over the data fewer) and is applied
+ * with rcqr_implicit_q_times / rcqr_implicit_qt_times.  Workspace and errors as
+ * rcqr_factor with variant RCQR_DIRECT2. */
+rcqr_status rcqr_factor_implicit(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                                 uint64_t seed, void *Q1, int64_t ldq, double *R, int64_t ldr, double *Rp,
+                                 int64_t ldrp, void *workspace, size_t ws_bytes, int *dev_status,
+                                 cudaStream_t stream);
+
+/* Products of the implicit Q = Q1 R'^{-1} (prec RCQR_F64: Q1, Z/B double; RCQR_F32: float):
+ *   rcqr_implicit_q_times:  Z = Q Y = Q1 (R'^{-1} Y), Y n x c double, Z m x c (Q1's type);
+ *   rcqr_implicit_qt_times: Z = Q^T B = R'^{-T} (Q1^T B), B m x c (Q1's type), Z n x c double
+ *     (the products summed in FP64 per row range, the ranges added in a fixed order).
+ * Limits: n, c <= 256, n c <= 8192.  Workspace: rcqr_implicit_workspace_size(m, n, c). */
+size_t rcqr_implicit_workspace_size(int64_t m, int64_t n, int64_t c);
+rcqr_status rcqr_implicit_q_times(const void *Q1, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                  int64_t ldrp, const double *Y, int64_t ldy, int64_t c, void *Z, int64_t ldz,
+                                  void *workspace, size_t ws_bytes, cudaStream_t stream);
+rcqr_status rcqr_implicit_qt_times(const void *Q1, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                   int64_t ldrp, const void *B, int64_t ldb, int64_t c, double *Z, int64_t ldz,
+                                   void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Column-oriented RCholeskyQR, Alg. 4 (Sec. 3.3), one block of columns per call, for X
+ * whose columns arrive in blocks (e.g. a Krylov basis built from the previous Q):
+ * block i is the m x b matrix Xi, holding columns i0 .. i0+b-1 of X; Q (m x n, Q's
+ * type by prec), S (k x n double) and R (n x n double) hold the earlier blocks' results
+ * (columns < i0; R's leading i0 x i0 block).  The call computes
+ *   P_i = Theta Xi;  R[:i0, i0:i0+b] = S[:, :i0]^+ P_i;
+ *   [S_i, R_ii] = QR(P_i - S[:, :i0] R[:i0, i0:i0+b])  (S_i -> S[:, i0:i0+b], diag >= 0);
+ *   Q[:, i0:i0+b] = (Xi - Q[:, :i0] R[:i0, i0:i0+b]) R_ii^{-1},
+ * steps 3-4 as one Householder QR of the stacked [S[:, :i0] | P_i]; rows i0.. of R[:, :i0]
+ * are set to 0.  rgs != 0: the randomized Gram-Schmidt form (remark after Alg. 4), S_i is
+ * replaced by Theta Q_i.  Limits: 1 <= b <= 64, i0 + b <= min(256, k), k a multiple of 8.
+ * Workspace: rcqr_colblock_workspace_size(m, b, k, i0, prec).  rcqr_factor_colwise runs
+ * every block of a given X (widths b, the last one narrower) in order. */
+size_t rcqr_colblock_workspace_size(int64_t m, int64_t b, int64_t k, int64_t i0, int prec);
+rcqr_status rcqr_colblock_step(const void *Xi, int64_t m, int64_t b, int64_t ldx, int prec, int64_t k, uint64_t seed,
+                               int64_t i0, int rgs, void *Q, int64_t ldq, double *S, int64_t lds, double *R,
+                               int64_t ldr, void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+rcqr_status rcqr_factor_colwise(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k, uint64_t seed,
+                                int64_t b, int rgs, void *Q, int64_t ldq, double *S, int64_t lds, double *R,
+                                int64_t ldr, void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream);
+
 /* Reduced RCholeskyQR, Alg. 5:  P = Theta X, Y = L X, [S, R] = QR(P),
  * Z = Y R^{-1}.  L: l x m double extractor (ldl >= l), or NULL for L = Theta
  * (then l must equal k and Z = P R^{-1}, the sketch of Q).  Z: l x n,

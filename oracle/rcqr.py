@@ -94,6 +94,55 @@ def rcholqr2(X, k, seed, stream=0, dist=GAUSSIAN):
     return Q2, R2, S
 
 
+def rcholqr2_implicit(X, k, seed, stream=0, dist=GAUSSIAN):
+    """Alg. 3 without step 4 (the remark after Alg. 3): returns (Q1, R, Rp) with Q1 from Alg. 2,
+    R = Rp R1 and the orthonormal factor Q = Q1 Rp^{-1} left implicit."""
+    Q1, _, R1 = rcholqr(X, k, seed, stream, dist)
+    Rp = linalg.cholesky(Q1.T @ Q1)
+    return Q1, Rp @ R1, Rp
+
+
+def implicit_q_times(Q1, Rp, Y):
+    """Q Y = Q1 (Rp^{-1} Y): the right product of the implicit Q."""
+    return np.asarray(Q1, dtype=np.float64) @ linalg.back_substitution_upper(Rp, np.asarray(Y, dtype=np.float64))
+
+
+def implicit_qt_times(Q1, Rp, B):
+    """Q^T B = Rp^{-T} (Q1^T B): the left product of the implicit Q (Q^T = Rp^{-T} Q1^T),
+    Rp^{-T} applied by forward substitution (rows of Rp^T = columns of Rp)."""
+    C = np.asarray(Q1, dtype=np.float64).T @ np.asarray(B, dtype=np.float64)
+    return linalg.forward_substitution(C.T, Rp).T
+
+
+def col_rcholqr(X, b, k, seed, rgs=False, stream=0):
+    """Alg. 4 (column-oriented RCholeskyQR) on X given as column blocks of width b (the last may be
+    narrower): for each block i, in the paper's steps,
+        2.  P_i = Theta X_i
+        3.  R_{<i,i} = S_{<i}^+ P_i              (least squares; a library routine)
+        4.  [S_i, R_ii] = QR(P_i - S_{<i} R_{<i,i})
+        5.  Q_i = (X_i - Q_{<i} R_{<i,i}) R_ii^{-1}   (forward substitution)
+    rgs=True turns it into the randomized Gram-Schmidt of the remark after Alg. 4: the sketch of
+    each computed block replaces S_i, S_i <- Theta Q_i.  Returns (Q, S, R)."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    Q = np.zeros((m, n))
+    S = np.zeros((k, n))
+    R = np.zeros((n, n))
+    for c0 in range(0, n, b):
+        c1 = min(n, c0 + b)
+        Xi = X[:, c0:c1]
+        Pi = sketch(Xi, k, seed, stream=stream)
+        if c0 > 0:
+            R[:c0, c0:c1] = np.linalg.lstsq(S[:, :c0], Pi, rcond=None)[0]
+        Si, Rii = linalg.householder_qr(Pi - S[:, :c0] @ R[:c0, c0:c1])
+        S[:, c0:c1] = Si
+        R[c0:c1, c0:c1] = Rii
+        Q[:, c0:c1] = linalg.forward_substitution(Xi - Q[:, :c0] @ R[:c0, c0:c1], Rii)
+        if rgs:
+            S[:, c0:c1] = sketch(Q[:, c0:c1], k, seed, stream=stream)
+    return Q, S, R
+
+
 def reduced(X, k, seed, L=None):
     """Alg. 5: returns (Z, S, R); L is an explicit l x m extractor, or None for L = Theta (then Z ~ S)."""
     X = np.asarray(X, dtype=np.float64)

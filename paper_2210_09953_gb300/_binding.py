@@ -52,6 +52,18 @@ _SIGS = {
                            _vp, _vp, _vp, _sz, _vp, _vp]),
     "rcqr_factor_theta": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i32, _i32, _dbl, _vp, _i64, _vp,
                                  _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rcqr_factor_implicit": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                                    _sz, _vp, _vp]),
+    "rcqr_implicit_workspace_size": (_sz, [_i64, _i64, _i64]),
+    "rcqr_implicit_q_times": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _sz,
+                                     _vp]),
+    "rcqr_implicit_qt_times": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _sz,
+                                      _vp]),
+    "rcqr_colblock_workspace_size": (_sz, [_i64, _i64, _i64, _i64, _i32]),
+    "rcqr_colblock_step": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _i32, _vp, _i64, _vp, _i64, _vp,
+                                  _i64, _vp, _sz, _vp, _vp]),
+    "rcqr_factor_colwise": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _i64, _i32, _vp, _i64, _vp, _i64, _vp,
+                                   _i64, _vp, _sz, _vp, _vp]),
     "rcqr_reduced": (_i32, [_vp, _i64, _i64, _i64, _i32, _i64, _u64, _vp, _i64, _i64, _vp, _i64, _vp,
                             _i64, _vp, _i64, _vp, _sz, _vp, _vp]),
 }
@@ -273,6 +285,81 @@ def rcqr_factor(X, k, seed, variant=DIRECT2, tau=0.0, Q=None, workspace=None, R=
                                                           float(tau), _ptr(Q), _ld(Q), _ptr(R), _ld(R), _ptr(perm),
                                                           _ptr(rank), wp, wb, _ptr(status), _stream()))
     return Q, R, perm, rank, status
+
+
+def rcqr_factor_implicit(X, k, seed, Q1=None, workspace=None):
+    """RCholeskyQR2 without its last substitution: returns (Q1, R, Rp, status), Q = Q1 Rp^{-1}."""
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    dev = X.device
+    if Q1 is None:
+        Q1 = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, dev)
+    R = colmajor(n, n, torch.float64, dev)
+    Rp = colmajor(n, n, torch.float64, dev)
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    ws = workspace if workspace is not None else _workspace(rcqr_workspace_size(m, n, k, DIRECT2, prec), dev)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_factor_implicit", lib.rcqr_factor_implicit(_ptr(X), m, n, _ld(X), prec, k, seed, _ptr(Q1), _ld(Q1),
+                                                            _ptr(R), _ld(R), _ptr(Rp), _ld(Rp), wp, wb, _ptr(status),
+                                                            _stream()))
+    return Q1, R, Rp, status
+
+
+def rcqr_implicit_q_times(Q1, Rp, Y):
+    """Z = Q Y = Q1 (Rp^{-1} Y) (m x c, Q1's type); Y n x c float64."""
+    m, n = Q1.shape
+    c = Y.shape[1]
+    prec = F64 if Q1.dtype == torch.float64 else F32
+    Z = colmajor(m, c, Q1.dtype, Q1.device)
+    ws = _workspace(lib.rcqr_implicit_workspace_size(m, n, c), Q1.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_implicit_q_times", lib.rcqr_implicit_q_times(_ptr(Q1), m, n, _ld(Q1), prec, _ptr(Rp), _ld(Rp),
+                                                              _ptr(Y), _ld(Y), c, _ptr(Z), _ld(Z), wp, wb, _stream()))
+    return Z
+
+
+def rcqr_implicit_qt_times(Q1, Rp, B):
+    """Z = Q^T B = Rp^{-T} (Q1^T B) (n x c, float64); B m x c of Q1's type."""
+    m, n = Q1.shape
+    c = B.shape[1]
+    prec = F64 if Q1.dtype == torch.float64 else F32
+    Z = colmajor(n, c, torch.float64, Q1.device)
+    ws = _workspace(lib.rcqr_implicit_workspace_size(m, n, c), Q1.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_implicit_qt_times", lib.rcqr_implicit_qt_times(_ptr(Q1), m, n, _ld(Q1), prec, _ptr(Rp), _ld(Rp),
+                                                                _ptr(B), _ld(B), c, _ptr(Z), _ld(Z), wp, wb, _stream()))
+    return Z
+
+
+def rcqr_factor_colwise(X, k, seed, b, rgs=False):
+    """Alg. 4 over the column blocks of X (width b): returns (Q, S, R, status)."""
+    m, n = X.shape
+    prec = prec_of(X.dtype)
+    dev = X.device
+    Q = colmajor(m, n, torch.float64 if prec == F64 else torch.float32, dev)
+    S = colmajor(k, n, torch.float64, dev)
+    R = torch.zeros((n, n), dtype=torch.float64, device=dev).t()
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    need = max(int(lib.rcqr_colblock_workspace_size(m, min(b, n - i0), k, i0, prec)) for i0 in range(0, n, b))
+    ws = _workspace(need, dev)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_factor_colwise", lib.rcqr_factor_colwise(_ptr(X), m, n, _ld(X), prec, k, seed, b, int(rgs), _ptr(Q),
+                                                          _ld(Q), _ptr(S), _ld(S), _ptr(R), _ld(R), wp, wb,
+                                                          _ptr(status), _stream()))
+    return Q, S, R, status
+
+
+def rcqr_colblock_step(Xi, k, seed, i0, Q, S, R, rgs=False):
+    """One block of Alg. 4 into the caller's (Q, S, R); returns status."""
+    m, b = Xi.shape
+    prec = prec_of(Xi.dtype)
+    status = torch.zeros(2, dtype=torch.int32, device=Xi.device)
+    ws = _workspace(lib.rcqr_colblock_workspace_size(m, b, k, i0, prec), Xi.device)
+    wp, wb = _aligned_ptr(ws)
+    _check("rcqr_colblock_step", lib.rcqr_colblock_step(_ptr(Xi), m, b, _ld(Xi), prec, k, seed, i0, int(rgs), _ptr(Q),
+                                                        _ld(Q), _ptr(S), _ld(S), _ptr(R), _ld(R), wp, wb,
+                                                        _ptr(status), _stream()))
+    return status
 
 
 def rcqr_reduced(X, k, seed, L=None, want_S=True):

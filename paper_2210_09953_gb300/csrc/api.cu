@@ -263,7 +263,8 @@ namespace rcqr {
 rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
                         uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
-                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream, int dist) {
+                        void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream, int dist,
+                        double *Rp_out, int64_t ldrp) {
   if (!X || !Q || !R || !dev_status || !valid_prec(prec) || !valid_sizes(m, n, k) || ldx < m ||
       ldq < m || ldr < n || variant < 0 || variant > 5)
     return RCQR_EINVAL;
@@ -321,9 +322,12 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
     RCQR_TRY(launch_trsm(X, m, n, ldx, prec, R, ldr, pm, rkp, Q, ldq, *scratch(), stream, dev_status));
   }
   if (pass2) {
-    // Alg. 3 steps 2-4 on the computed Q
+    // Alg. 3 steps 2-4 on the computed Q (implicit Q: steps 2-3 only, R' returned)
     if (!fused) RCQR_TRY(launch_gram(Q, m, n, ldq, qprec, rkp, b.A, n, *scratch(), stream));
-    RCQR_TRY(launch_cholqr_pass(b.A, n, rkp, b.Rp, R, ldr, Q, m, ldq, qprec, *scratch(), stream, dev_status));
+    if (Rp_out)
+      RCQR_TRY(launch_chol_update(b.A, n, n, rkp, Rp_out, ldrp, R, ldr, dev_status, stream));
+    else
+      RCQR_TRY(launch_cholqr_pass(b.A, n, rkp, b.Rp, R, ldr, Q, m, ldq, qprec, *scratch(), stream, dev_status));
   }
 #undef RCQR_TRY
   return RCQR_OK;
@@ -412,5 +416,41 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
 }
 
 uint32_t rcqr_set_wait_polls(uint32_t polls) { return set_wait_polls(polls); }
+
+rcqr_status rcqr_factor_implicit(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, int64_t k,
+                                 uint64_t seed, void *Q1, int64_t ldq, double *R, int64_t ldr, double *Rp,
+                                 int64_t ldrp, void *workspace, size_t ws_bytes, int *dev_status,
+                                 cudaStream_t stream) {
+  if (!Rp || ldrp < n) return RCQR_EINVAL;
+  return rcqr::factor_impl(X, m, n, ldx, prec, k, seed, 0u, RCQR_DIRECT2, 0.0, Q1, ldq, R, ldr, nullptr, nullptr,
+                           workspace, ws_bytes, dev_status, stream, RCQR_THETA_GAUSSIAN, Rp, ldrp);
+}
+
+size_t rcqr_implicit_workspace_size(int64_t m, int64_t n, int64_t c) {
+  if (m < 1 || !implicit_sizes_ok(n, c)) return 0;
+  return implicit_workspace(m, n, c) + 512;
+}
+
+rcqr_status rcqr_implicit_q_times(const void *Q1, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                  int64_t ldrp, const double *Y, int64_t ldy, int64_t c, void *Z, int64_t ldz,
+                                  void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!Q1 || !Rp || !Y || !Z || !(prec == RCQR_F64 || prec == RCQR_F32) || m < 1 || !implicit_sizes_ok(n, c) ||
+      ldq < m || ldrp < n || ldy < n || ldz < m)
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < implicit_workspace(m, n, c)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_implicit_q_times(Q1, m, n, ldq, prec, Rp, ldrp, Y, ldy, c, Z, ldz, w, stream));
+}
+
+rcqr_status rcqr_implicit_qt_times(const void *Q1, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                   int64_t ldrp, const void *B, int64_t ldb, int64_t c, double *Z, int64_t ldz,
+                                   void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (!Q1 || !Rp || !B || !Z || !(prec == RCQR_F64 || prec == RCQR_F32) || m < 1 || !implicit_sizes_ok(n, c) ||
+      ldq < m || ldrp < n || ldb < m || ldz < n)
+    return RCQR_EINVAL;
+  if (!workspace || !aligned(workspace) || ws_bytes < implicit_workspace(m, n, c)) return RCQR_EWORKSPACE;
+  Workspace w(workspace, ws_bytes);
+  return cuda_status(launch_implicit_qt_times(Q1, m, n, ldq, prec, Rp, ldrp, B, ldb, c, Z, ldz, w, stream));
+}
 
 }  // extern "C"

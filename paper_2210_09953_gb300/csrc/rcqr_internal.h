@@ -56,7 +56,7 @@ rcqr_status factor_impl(const void *X, int64_t m, int64_t n, int64_t ldx, int pr
                         uint64_t seed, uint32_t stream_id, int variant, double tau, void *Q,
                         int64_t ldq, double *R, int64_t ldr, int32_t *perm, int64_t *rank,
                         void *workspace, size_t ws_bytes, int *dev_status, cudaStream_t stream,
-                        int dist = RCQR_THETA_GAUSSIAN);
+                        int dist = RCQR_THETA_GAUSSIAN, double *Rp_out = nullptr, int64_t ldrp = 0);
 
 // f of the strong rank-revealing QR in the RCQR_SRR / RCQR_SRR2 variants (Sec. 4, Sec. 6.1).
 constexpr double kStrongRrqrF = 1.5;
@@ -168,6 +168,21 @@ int trsm_tc_gram_groups(int64_t m);
 cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
                            const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
                            double *partial, int *status, cudaStream_t st);
+// The implicit Q of RCholeskyQR2 (implicit.cu): Z = Q1 (R'^{-1} Y) and Z = R'^{-T} (Q1^T B).
+bool implicit_sizes_ok(int64_t n, int64_t c);
+size_t implicit_workspace(int64_t m, int64_t n, int64_t c);
+cudaError_t launch_implicit_q_times(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                    int64_t ldrp, const double *Y, int64_t ldy, int64_t c, void *Z, int64_t ldz,
+                                    Workspace &ws, cudaStream_t st);
+cudaError_t launch_implicit_qt_times(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *Rp,
+                                     int64_t ldrp, const void *B, int64_t ldb, int64_t c, double *Z, int64_t ldz,
+                                     Workspace &ws, cudaStream_t st);
+// Column-oriented RCholeskyQR, one block (colwise.cu).
+bool colblock_sizes_ok(int64_t m, int64_t b, int64_t k, int64_t i0);
+size_t colblock_workspace(int64_t m, int64_t b, int64_t k, int64_t i0, int prec);
+cudaError_t colblock_step(const void *Xi, int64_t m, int64_t b, int64_t ldx, int prec, int64_t k, uint64_t seed,
+                          int64_t i0, int rgs, void *Q, int64_t ldq, double *S, int64_t lds, double *R, int64_t ldr,
+                          Workspace &ws, cudaStream_t st, int *dev_status);
 // A = sum of `groups` n x n partials (fixed order), trsm_simt.cu.
 cudaError_t launch_gram_reduce(const double *partial, int groups, int64_t n, double *A, int64_t lda,
                                cudaStream_t st);

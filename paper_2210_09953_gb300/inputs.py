@@ -105,3 +105,13 @@ def batched_shapes(count, seed, m_lo=16384, m_hi=262144, n_choices=(16, 32, 64, 
     ms = torch.randint(m_lo, m_hi + 1, (count,), generator=g).tolist()
     ns = torch.randint(0, len(n_choices), (count,), generator=g).tolist()
     return [(int(mm), int(n_choices[j])) for mm, j in zip(ms, ns)]
+
+
+def e2_matrix(m, n, dtype="f64", device="cpu", ld=None):
+    """The second test matrix of Sec. 6.1: X_ij = sin(10 (x_i + y_j)) / (cos(100 (y_j - x_i)) + 1.1)
+    on the uniform unit grid x_i = i / (m - 1), y_j = j / (n - 1), built in FP64 and rounded to
+    ``dtype``; column-major.  Its singular values decay rapidly (numerically low rank)."""
+    x = torch.arange(m, dtype=torch.float64, device=device) / max(m - 1, 1)
+    y = torch.arange(n, dtype=torch.float64, device=device) / max(n - 1, 1)
+    X = torch.sin(10 * (x[:, None] + y[None, :])) / (torch.cos(100 * (y[None, :] - x[:, None])) + 1.1)
+    return to_colmajor(X, _DT[dtype], ld)

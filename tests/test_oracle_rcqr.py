@@ -242,3 +242,55 @@ def test_rcholqr2_with_rademacher_theta():
     _, Rh = linalg.householder_qr(X)
     assert rcqr.orthogonality(Q) <= 100 * n * U64
     assert np.max(np.abs(R - Rh) / np.abs(Rh).max(axis=0)[None, :]) <= 10 * n * U64 * kappa
+
+
+def test_implicit_rcholqr2_is_the_explicit_one():
+    # Alg. 3 without step 4: Q1 Rp^{-1} is the Q of Alg. 3 (the same substitution), R the same R,
+    # and the two products of the implicit Q agree with the explicit Q
+    m, n, k, kappa = 2500, 9, 72, 1e7
+    X, _ = svd_matrix(m, n, kappa, 31)
+    Q, R, _ = rcqr.rcholqr2(X, k, 17)
+    Q1, R2, Rp = rcqr.rcholqr2_implicit(X, k, 17)
+    assert np.array_equal(R2, R)
+    assert np.array_equal(linalg.forward_substitution(Q1, Rp), Q)
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((n, 4))
+    B = rng.standard_normal((m, 3))
+    assert np.linalg.norm(rcqr.implicit_q_times(Q1, Rp, Y) - Q @ Y) <= 1e-12 * np.linalg.norm(Y)
+    assert np.linalg.norm(rcqr.implicit_qt_times(Q1, Rp, B) - Q.T @ B) <= 1e-12 * np.linalg.norm(B)
+    # a transposed Rp in the left product is caught
+    bad = linalg.forward_substitution((Q1.T @ B).T, Rp.T.copy()).T
+    assert np.linalg.norm(bad - Q.T @ B) > 1e-6 * np.linalg.norm(B)
+
+
+def test_column_oriented_rcholqr_one_block_is_rcholqr():
+    # Alg. 4 with a single block is Alg. 2 step by step
+    m, n, k = 2000, 8, 64
+    X, _ = svd_matrix(m, n, 1e5, 41)
+    Q, S, R = rcqr.col_rcholqr(X, n, k, 9)
+    Q2, S2, R2 = rcqr.rcholqr(X, k, 9)
+    assert np.array_equal(R, R2) and np.array_equal(S, S2) and np.array_equal(Q, Q2)
+
+
+@pytest.mark.parametrize("rgs", [False, True])
+@pytest.mark.parametrize("kappa", [1e3, 1e9])
+def test_column_oriented_rcholqr_matches_thm_5_2(rgs, kappa):
+    # "numerically equivalent to Alg. 2": block by block, the same Thm. 5.2 statements hold
+    m, n, k, b = 3000, 12, 192, 4
+    X, U = svd_matrix(m, n, kappa, 43)
+    Q, S, R = rcqr.col_rcholqr(X, b, k, 77, rgs=rgs)
+    assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
+    assert np.all(np.linalg.norm(Q @ R - X, axis=0) <= 2.1 * U64 * n * np.linalg.norm(X, axis=0) * 10)
+    Th = theta.theta(77, k, 0, m)
+    eps = rcqr.embedding_epsilon(Th, U)
+    s = np.linalg.svd(Q, compute_uv=False)
+    slack = 4 * U64 * n ** 1.5 * kappa
+    assert s.min() >= (1 + eps) ** -0.5 - slack and s.max() <= (1 - eps) ** -0.5 + slack
+    # the same R as Alg. 2 up to its forward error (the blocks are solved in the same order)
+    _, _, R2 = rcqr.rcholqr(X, k, 77)
+    assert np.max(np.abs(R - R2) / np.abs(R2).max(axis=0)[None, :]) <= 10 * n * U64 * kappa + 1e-13
+    if rgs:
+        assert np.linalg.norm(S - Th @ Q) <= 1e-12 * np.sqrt(n)        # S is the sketch of Q
+    else:
+        # S orthonormal up to the loss of the one-projection (least-squares) step, O(n u kappa)
+        assert np.linalg.norm(S.T @ S - np.eye(n)) <= 100 * n * U64 * kappa
