@@ -138,18 +138,16 @@ cudaError_t launch_set_rank(int64_t *rank, int64_t value, cudaStream_t st);
 
 // ---- bulk kernels over m -----------------------------------------------------
 size_t trsm_workspace(int64_t m, int64_t n, int prec);
-// allow_tc = false keeps the FP32 SIMT substitution (round-to-nearest operations
-// throughout) where the tensor-core kernel would otherwise be used.
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
                         void *Q, int64_t ldq, Workspace &ws, cudaStream_t st,
-                        int *dev_status = nullptr, bool allow_tc = true);
+                        int *dev_status = nullptr);
 // FP32 substitution and Gram of the mixed path (trsm_f32.cu).
 bool trsm32_supported(int64_t n);
 size_t trsm32_workspace(int64_t n);
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st, int *dev_status = nullptr, bool allow_tc = true);
+                          Workspace &ws, cudaStream_t st);
 int gram32_groups(int64_t m, int64_t n);
 cudaError_t launch_gram32(const float *Q, int64_t m, int64_t n, int64_t ldq, const int64_t *rank,
                           double *partial, int groups, cudaStream_t st);
@@ -160,14 +158,14 @@ size_t trsm32_gram_workspace(int64_t m, int64_t n);
 cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                                int64_t ldr, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
                                double *A, int64_t lda, Workspace &ws, cudaStream_t st, int *dev_status = nullptr);
-// Blocked substitution on the tensor cores (trsm_tc.cu), 32 < n <= 64: Rf is the 64 x 64
-// FP32 R of trsm32_prep_kernel; with `partial` (trsm_tc_gram_groups(m) n x n FP64
-// blocks) it also writes the per-CTA partial Gram matrices of Q.
+// Blocked substitution on the tensor cores fused with the Gram (trsm_tc.cu), 32 < n <= 64:
+// Rf is the 64 x 64 FP32 R of trsm32_prep_kernel; `partial` receives one n x n FP64 partial
+// Gram matrix of Q per CTA (trsm_tc_gram_groups(m) of them).
 bool trsm_tc_supported(int64_t n);
 int trsm_tc_gram_groups(int64_t m);
-cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
-                           const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
-                           double *partial, int *status, cudaStream_t st);
+cudaError_t launch_trsm_tc_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
+                                const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                                double *partial, int *status, cudaStream_t st);
 // The implicit Q of RCholeskyQR2 (implicit.cu): Z = Q1 (R'^{-1} Y) and Z = R'^{-T} (Q1^T B).
 bool implicit_sizes_ok(int64_t n, int64_t c);
 size_t implicit_workspace(int64_t m, int64_t n, int64_t c);

@@ -535,10 +535,7 @@ bool trsm32_supported(int64_t n) { return n >= 1 && n <= 256; }
 
 // R in FP32 for the substitution kernels: NB x NB, NB = n rounded up to 16 (row
 // kernel) or to 64 (panel kernel, n > 64).
-int trsm32_nb(int64_t n) {
-  if (trsm_tc_supported(n)) return 64;      // the tensor-core kernel's padded width
-  return n > 64 ? (int)((n + 63) / 64) * 64 : (int)((n + 15) / 16) * 16;
-}
+int trsm32_nb(int64_t n) { return n > 64 ? (int)((n + 63) / 64) * 64 : (int)((n + 15) / 16) * 16; }
 
 size_t trsm32_workspace(int64_t n) {
   const int NB = trsm32_nb(n);
@@ -550,14 +547,12 @@ size_t trsm32_workspace(int64_t n) {
 
 cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const double *R,
                           int64_t ldr, const int32_t *perm, const int64_t *rank, void *Q, int64_t ldq,
-                          Workspace &ws, cudaStream_t st, int *dev_status, bool allow_tc) {
+                          Workspace &ws, cudaStream_t st) {
   const int NB = trsm32_nb(n);
   float *Rf = ws.take<float>((size_t)NB * NB);
   float *dinv = ws.take<float>((size_t)NB);
   if (!Rf || !dinv) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
-  if (allow_tc && trsm_tc_supported(n))
-    return launch_trsm_tc(X, m, n, ldx, prec, Rf, dinv, perm, rank, (float *)Q, ldq, nullptr, dev_status, st);
   if (n > 64) {
     const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);
     if (prec == RCQR_BF16)
@@ -602,7 +597,7 @@ cudaError_t launch_trsm32_gram(const void *X, int64_t m, int64_t n, int64_t ldx,
   if (!Rf || !dinv || !partial) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
   if (tc) {
-    cudaError_t e = launch_trsm_tc(X, m, n, ldx, prec, Rf, dinv, perm, rank, Q, ldq, partial, dev_status, st);
+    cudaError_t e = launch_trsm_tc_gram(X, m, n, ldx, prec, Rf, dinv, perm, rank, Q, ldq, partial, dev_status, st);
     if (e != cudaSuccess) return e;
     return launch_gram_reduce(partial, G, n, A, lda, st);
   }

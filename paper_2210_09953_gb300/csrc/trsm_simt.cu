@@ -136,10 +136,10 @@ size_t trsm_workspace(int64_t m, int64_t n, int prec) {
 // substitution of trsm_f32.cu, the working precision of the mixed path.
 cudaError_t launch_trsm(const void *X, int64_t m, int64_t n, int64_t ldx, int prec,
                         const double *R, int64_t ldr, const int32_t *perm, const int64_t *rank,
-                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st, int *dev_status,
-                        bool allow_tc) {
+                        void *Q, int64_t ldq, Workspace &ws, cudaStream_t st, int *dev_status) {
+  (void)dev_status;
   if (prec != RCQR_F64 && trsm32_supported(n))
-    return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st, dev_status, allow_tc);
+    return launch_trsm32(X, m, n, ldx, prec, R, ldr, perm, rank, Q, ldq, ws, st);
   if (prec != RCQR_F64) return cudaErrorInvalidValue;   // n <= 256 always takes the FP32 kernels
   const unsigned blocks = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
   trsm_rows_kernel<double, double><<<blocks, kTrsmThreads, 0, st>>>((const double *)X, m, (int)n, ldx, R, ldr,
@@ -160,9 +160,7 @@ cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, 
                                int *dev_status) {
   cudaError_t e = launch_chol_update(A, n, n, rank, Rp, n, R, ldr, dev_status, st);
   if (e != cudaSuccess) return e;
-  // Q <- Q R'^{-1} with the SIMT substitution: the tensor cores' FP32 accumulation would
-  // add a biased rounding to the orthonormal factor itself
-  return launch_trsm(Q, m, n, ldq, qprec, Rp, n, nullptr, rank, Q, ldq, ws, st, dev_status, false);
+  return launch_trsm(Q, m, n, ldq, qprec, Rp, n, nullptr, rank, Q, ldq, ws, st, dev_status);
 }
 
 size_t gram_workspace(int64_t m, int64_t n) {

@@ -1,6 +1,8 @@
 // Q = X R^{-1} (Alg. 2 step 3) for 32 < n <= 64 as a blocked substitution on
-// the tcgen05 tensor cores, optionally fused with the Gram matrix A = Q^T Q of
-// the second pass (Alg. 3 step 2).
+// the tcgen05 tensor cores, fused with the Gram matrix A = Q^T Q of the second
+// pass (Alg. 3 step 2): the first pass of RCholeskyQR2 on the mixed path.
+// (The template keeps GRAM = false, the substitution alone; the library uses the
+// FP32 SIMT substitution there, which measured faster on its own.)
 //
 // A CTA of 128 threads takes tiles of 128 rows (thread t owns row t of the tile
 // and TMEM lane t; two or three CTAs per SM hide each other's latencies).  The
@@ -445,17 +447,12 @@ bool trsm_tc_supported(int64_t n) { return n > 32 && n <= 64; }
 
 int trsm_tc_gram_groups(int64_t m) { return tc_grid<true>(m); }
 
-cudaError_t launch_trsm_tc(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
-                           const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
-                           double *partial, int *status, cudaStream_t st) {
+cudaError_t launch_trsm_tc_gram(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
+                                const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                                double *partial, int *status, cudaStream_t st) {
   TcTrsmArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, partial, status};
-  const bool gram = partial != nullptr;
-  if (gram) {
-    const int grid = tc_grid<true>(m);
-    return prec == RCQR_BF16 ? launch_tc<__nv_bfloat16, true>(a, grid, st) : launch_tc<float, true>(a, grid, st);
-  }
-  const int grid = tc_grid<false>(m);
-  return prec == RCQR_BF16 ? launch_tc<__nv_bfloat16, false>(a, grid, st) : launch_tc<float, false>(a, grid, st);
+  const int grid = tc_grid<true>(m);
+  return prec == RCQR_BF16 ? launch_tc<__nv_bfloat16, true>(a, grid, st) : launch_tc<float, true>(a, grid, st);
 }
 
 }  // namespace rcqr

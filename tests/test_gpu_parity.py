@@ -330,16 +330,21 @@ def test_reduced_parity(rc, inputs, use_L):
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("m,n", [(70001, 64), (5000, 17), (300, 48)])
 def test_trsm_gram_fused_matches_separate_steps(rc, inputs, prec, m, n):
-    """The fused pass: Q bit-identical to rcqr_trsm (same substitution arithmetic), A within the
-    compensated-Gram bound of the oracle Gram of that Q."""
+    """The fused pass: Q within the FP32 substitution's backward error (bit-identical to rcqr_trsm
+    where both use the SIMT substitution, n <= 32), A within the compensated-Gram bound of the
+    oracle Gram of that Q."""
     X = inputs.svd_matrix(m, n, 1e6, 900 + n, dtype=prec, device=DEV)
     k = (4 * n + 7) // 8 * 8
     R0 = rc.rcqr_small_qr(rc.rcqr_sketch(X, k, 77), want_S=False)
     Q, A = rc.rcqr_trsm_gram(X, R0)
     Qs = rc.rcqr_trsm(X, R0)
     torch.cuda.synchronize()
-    assert torch.equal(Q, Qs)
+    if n <= 32:
+        assert torch.equal(Q, Qs)
     Qh = host64(Q)
+    Ro = host64(R0)
+    E = np.abs(host64(X) - Qh @ Ro)
+    assert np.all(E <= 2 * (n + 3) * 2.0 ** -24 * (np.abs(Qh) @ np.abs(Ro)) + 1e-300)
     Ao = Qh.T @ Qh
     scale = np.abs(Qh).T @ np.abs(Qh)
     assert np.all(np.abs(host64(A) - Ao) <= 66 * 2.0 ** -24 * scale)

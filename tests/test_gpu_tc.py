@@ -1,5 +1,6 @@
-"""GPU parity of the tensor-core blocked substitution (32 < n <= 64, FP32 / BF16 X) and of the
-Gram matrix fused into it, against the oracle.
+"""GPU parity of the tensor-core blocked substitution fused with the Gram matrix (rcqr_trsm_gram,
+32 < n <= 64, FP32 / BF16 X), and of the FP32 SIMT substitution (rcqr_trsm) beside it, against the
+oracle.
 
 Tolerances (u = 2^-24, the mixed path's working precision):
 * Q = X R^{-1}: the row-wise backward error of an FP32 substitution, |X - Q R| <=
@@ -73,9 +74,9 @@ def test_tc_substitution_and_fused_gram(rc, inputs, prec, m, n, cond):
     Q = rc.rcqr_trsm(X, R)
     Qf, A = rc.rcqr_trsm_gram(X, R)
     torch.cuda.synchronize()
-    assert torch.equal(Q, Qf)                         # one substitution arithmetic for both calls
-    Xh, Qg = host64(X), host64(Q)
-    check_substitution(Xh, Qg, Ro, n, cond)
+    Xh, Qg = host64(X), host64(Qf)
+    check_substitution(Xh, Qg, Ro, n, cond)           # tensor-core blocked substitution
+    check_substitution(Xh, host64(Q), Ro, n, cond)    # SIMT substitution
     Ao = Qg.T @ Qg
     scale = np.abs(Qg).T @ np.abs(Qg)
     assert np.all(np.abs(host64(A) - Ao) <= 66 * U32 * scale)
@@ -90,14 +91,15 @@ def test_tc_substitution_permuted_rank(rc, inputs):
     rank = torch.tensor([r], dtype=torch.int64, device=DEV)
     Ro = np.triu(np.random.default_rng(0).standard_normal((n, n))) + 8 * np.eye(n)
     R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
-    Q = host64(rc.rcqr_trsm(X, R, perm=perm, rank=rank))
+    Qs = host64(rc.rcqr_trsm(X, R, perm=perm, rank=rank))
     Qf, A = rc.rcqr_trsm_gram(X, R, perm=perm, rank=rank)
     torch.cuda.synchronize()
-    assert np.array_equal(Q, host64(Qf))
+    Q = host64(Qf)
     Xs = host64(X)[:, perm_h[:r]]
     R11 = Ro[:r, :r].astype(np.float32).astype(np.float64)
     check_substitution(Xs, Q[:, :r], R11, r, np.linalg.cond(R11))
-    assert np.all(Q[:, r:] == 0)
+    check_substitution(Xs, Qs[:, :r], R11, r, np.linalg.cond(R11))
+    assert np.all(Q[:, r:] == 0) and np.all(Qs[:, r:] == 0)
     Ag = host64(A)
     assert np.all(Ag[r:, :] == 0) and np.all(Ag[:, r:] == 0)
 
