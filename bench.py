@@ -29,8 +29,8 @@ M, N, K, COND = 4194304, 64, 256, 1e8
 METRIC = "GB/s of X factored (RCholeskyQR2, mixed path: FP32 X) at stated ||Q^TQ-I||"
 
 
-def workload_name(m):
-    return f"rcholqr2 {m}x{N} k={K} cond 1e8 (U diag(sigma) V^T), X f32 column-major"
+def workload_name(m, n=N, k=K):
+    return f"rcholqr2 {m}x{n} k={k} cond 1e8 (U diag(sigma) V^T), X f32 column-major"
 
 
 SEED_X, SEED_THETA = 1002, 0x5EED0002
@@ -39,7 +39,9 @@ ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (abou
 # (dram__bytes_read.sum + dram__bytes_write.sum of every kernel of the call, captured on a
 # 1M-row launch and scaled by 4: per-row traffic is the same).  None where the kernels
 # changed after the last capture.
-TRAFFIC = {"sketch": None, "trsm": None, "trsm_gram": None}
+TRAFFIC = {"sketch": 4 * (268455680 + 190208 + 288155648 + 26288128 + 19934464),
+           "trsm_gram": 4 * (26624 + 268855552 + 225936384 + 6237696),
+           "trsm": 4 * (26880 + 268603648 + 204486656)}
 
 
 def parse():
@@ -49,9 +51,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--m", type=int, default=M)
+    p.add_argument("--n", type=int, default=N, help="columns (the default is the headline workload)")
+    p.add_argument("--k", type=int, default=K, help="sketch rows")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline oracle timing")
     p.add_argument("--no-variants", action="store_true", help="skip the timings of the other variants and sizes")
+    p.add_argument("--no-e2e", action="store_true", help="skip the streamed end-to-end measurement")
     return p.parse_args()
 
 
@@ -342,7 +347,7 @@ def run_ours(args):
     ms_trsm = timed(lambda: rc.rcqr_trsm(X32, R1, Q=Q32), max(3, args.steps), 2)
     # the dominant kernel of the step: the first substitution fused with the Gram (one launch
     # plus its R preparation and the Gram reduction)
-    ms_tg = timed(lambda: rc.rcqr_trsm_gram(X32, R1, Q=Q32, workspace=ws32), max(3, args.steps), 2)
+    ms_tg = timed(lambda: rc.rcqr_trsm_gram(X32, R1, Q=Q32, workspace=ws32), max(3, args.steps), 2) if N <= 64 else None
 
     fp64 = None
     if not args.no_fp64:
@@ -360,112 +365,120 @@ def run_ours(args):
                 "status": int(st64[0])}
         del Q64, ws64
 
-    # End to end through the public call, streaming: every step copies its X from pinned host
-    # memory, factors it and copies Q and R back.  Three device buffer sets (X, Q, R, rank,
-    # status and workspace each, allocated once, so no buffer changes hands between streams)
-    # on three streams let step s+1's upload, step s's factorization and step s-1's download
-    # run at the same time; every timed step's copies are inside the timed region.  Host
-    # buffers are flat pinned arrays viewed column-major, so each transfer is one copy.
-    Xh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
-    Xh_flat.view(N, m).t().copy_(X32)
-    Qh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
-    Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
-    NSETS = 3
-    bufs = []
-    for _ in range(NSETS):
-        Xd = rc.colmajor(m, N, torch.float32, dev)
-        Qd = rc.colmajor(m, N, torch.float32, dev)
-        Rd = rc.colmajor(N, N, torch.float64, dev)
-        rkd = torch.empty(1, dtype=torch.int64, device=dev)
-        std = torch.zeros(2, dtype=torch.int32, device=dev)
-        wsd = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.DIRECT2, rc.F32) + 256, dtype=torch.uint8,
-                          device=dev)
-        bufs.append((Xd, Xd.t().reshape(-1), Qd, Qd.t().reshape(-1), Rd, rkd, std, wsd))
-    s_in, s_run, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    e2e = None
+    if not args.no_e2e:
+        # End to end through the public call, streaming: every step copies its X from pinned host
+        # memory, factors it and copies Q and R back.  Three device buffer sets (X, Q, R, rank,
+        # status and workspace each, allocated once, so no buffer changes hands between streams)
+        # on three streams let step s+1's upload, step s's factorization and step s-1's download
+        # run at the same time; every timed step's copies are inside the timed region.  Host
+        # buffers are flat pinned arrays viewed column-major, so each transfer is one copy.
+        Xh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
+        Xh_flat.view(N, m).t().copy_(X32)
+        Qh_flat = torch.empty(N * m, dtype=torch.float32, pin_memory=True)
+        Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
+        NSETS = 3
+        bufs = []
+        for _ in range(NSETS):
+            Xd = rc.colmajor(m, N, torch.float32, dev)
+            Qd = rc.colmajor(m, N, torch.float32, dev)
+            Rd = rc.colmajor(N, N, torch.float64, dev)
+            rkd = torch.empty(1, dtype=torch.int64, device=dev)
+            std = torch.zeros(2, dtype=torch.int32, device=dev)
+            wsd = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.DIRECT2, rc.F32) + 256, dtype=torch.uint8,
+                              device=dev)
+            bufs.append((Xd, Xd.t().reshape(-1), Qd, Qd.t().reshape(-1), Rd, rkd, std, wsd))
+        s_in, s_run, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def e2e_steps(count, marks=None):
-        done_out = [None] * NSETS       # event: the buffer set's previous Q download finished
-        for s in range(count):
-            Xd, Xf, Qd, Qf, Rd, rkd, std, wsd = bufs[s % NSETS]
-            ev = {}
-            with torch.cuda.stream(s_in):
-                if done_out[s % NSETS] is not None:
-                    s_in.wait_event(done_out[s % NSETS])
+        def e2e_steps(count, marks=None):
+            done_out = [None] * NSETS       # event: the buffer set's previous Q download finished
+            for s in range(count):
+                Xd, Xf, Qd, Qf, Rd, rkd, std, wsd = bufs[s % NSETS]
+                ev = {}
+                with torch.cuda.stream(s_in):
+                    if done_out[s % NSETS] is not None:
+                        s_in.wait_event(done_out[s % NSETS])
+                    if marks is not None:
+                        ev["up0"] = torch.cuda.Event(enable_timing=True)
+                        ev["up0"].record(s_in)
+                    Xf.copy_(Xh_flat, non_blocking=True)
+                    up = torch.cuda.Event(enable_timing=marks is not None)
+                    up.record(s_in)
+                with torch.cuda.stream(s_run):
+                    s_run.wait_event(up)
+                    rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Qd, workspace=wsd, R=Rd, rank=rkd,
+                                   status=std)
+                    ran = torch.cuda.Event(enable_timing=marks is not None)
+                    ran.record(s_run)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ran)
+                    Qh_flat.copy_(Qf, non_blocking=True)
+                    Rh.copy_(Rd, non_blocking=True)
+                    dn = torch.cuda.Event(enable_timing=marks is not None)
+                    dn.record(s_out)
+                    done_out[s % NSETS] = dn
                 if marks is not None:
-                    ev["up0"] = torch.cuda.Event(enable_timing=True)
-                    ev["up0"].record(s_in)
-                Xf.copy_(Xh_flat, non_blocking=True)
-                up = torch.cuda.Event(enable_timing=marks is not None)
-                up.record(s_in)
-            with torch.cuda.stream(s_run):
-                s_run.wait_event(up)
-                rc.rcqr_factor(Xd, K, SEED_THETA, variant=rc.DIRECT2, Q=Qd, workspace=wsd, R=Rd, rank=rkd,
-                               status=std)
-                ran = torch.cuda.Event(enable_timing=marks is not None)
-                ran.record(s_run)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ran)
-                Qh_flat.copy_(Qf, non_blocking=True)
-                Rh.copy_(Rd, non_blocking=True)
-                dn = torch.cuda.Event(enable_timing=marks is not None)
-                dn.record(s_out)
-                done_out[s % NSETS] = dn
-            if marks is not None:
-                ev.update(up=up, ran=ran, dn=dn)
-                marks.append(ev)
+                    ev.update(up=up, ran=ran, dn=dn)
+                    marks.append(ev)
+            for st_ in (s_in, s_run, s_out):
+                stream.wait_stream(st_)
+
+        e2e_steps(NSETS)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(16, args.steps)
+        e0.record(stream)
         for st_ in (s_in, s_run, s_out):
-            stream.wait_stream(st_)
-
-    e2e_steps(NSETS)
-    torch.cuda.synchronize()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_e2e = max(16, args.steps)
-    e0.record(stream)
-    for st_ in (s_in, s_run, s_out):
-        st_.wait_stream(stream)
-    e2e_steps(n_e2e)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / n_e2e
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t[0])
-    # where the streamed steps' time goes (an untimed run with an event at every phase boundary):
-    # per step the upload, factorization and download intervals, and the mean period
-    marks = []
-    e2e_steps(6, marks)
-    torch.cuda.synchronize()
-    t0 = marks[0]["up0"]
-    tl = [{"up": (t0.elapsed_time(mk["up0"]), t0.elapsed_time(mk["up"])),
-           "run": (t0.elapsed_time(mk["up"]), t0.elapsed_time(mk["ran"])),
-           "down": (t0.elapsed_time(mk["ran"]), t0.elapsed_time(mk["dn"]))} for mk in marks]
-    period = (tl[-1]["down"][1] - tl[1]["down"][1]) / (len(tl) - 2)
-    Xf0, Qf0 = bufs[0][1], bufs[0][3]
-    ms_h2d = timed(lambda: Xf0.copy_(Xh_flat, non_blocking=True), 3, 1)
-    ms_d2h = timed(lambda: Qh_flat.copy_(Qf0, non_blocking=True), 3, 1)
-
-    def both():
-        with torch.cuda.stream(s_in):
-            Xf0.copy_(Xh_flat, non_blocking=True)
-        with torch.cuda.stream(s_out):
-            Qh_flat.copy_(bufs[1][3], non_blocking=True)
-        for st_ in (s_in, s_out):
-            stream.wait_stream(st_)
-
-    def both_timed():
-        for st_ in (s_in, s_out):
             st_.wait_stream(stream)
-        both()
-    ms_both = timed(both_timed, 3, 1)
-    e2e_timeline = {"period_ms": round(period, 3),
-                    "upload_ms": round(statistics.median(b - a for a, b in (t["up"] for t in tl)), 3),
-                    "factor_ms": round(statistics.median(b - a for a, b in (t["run"] for t in tl)), 3),
-                    "download_ms": round(statistics.median(b - a for a, b in (t["down"] for t in tl)), 3),
-                    "h2d_and_d2h_together_ms": round(ms_both, 3),
-                    "steps": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in t.items()} for t in tl]}
+        e2e_steps(n_e2e)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / n_e2e
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t[0])
+        # where the streamed steps' time goes (an untimed run with an event at every phase boundary):
+        # per step the upload, factorization and download intervals, and the mean period
+        marks = []
+        e2e_steps(6, marks)
+        torch.cuda.synchronize()
+        t0 = marks[0]["up0"]
+        tl = [{"up": (t0.elapsed_time(mk["up0"]), t0.elapsed_time(mk["up"])),
+               "run": (t0.elapsed_time(mk["up"]), t0.elapsed_time(mk["ran"])),
+               "down": (t0.elapsed_time(mk["ran"]), t0.elapsed_time(mk["dn"]))} for mk in marks]
+        period = (tl[-1]["down"][1] - tl[1]["down"][1]) / (len(tl) - 2)
+        Xf0, Qf0 = bufs[0][1], bufs[0][3]
+        ms_h2d = timed(lambda: Xf0.copy_(Xh_flat, non_blocking=True), 3, 1)
+        ms_d2h = timed(lambda: Qh_flat.copy_(Qf0, non_blocking=True), 3, 1)
+
+        def both():
+            with torch.cuda.stream(s_in):
+                Xf0.copy_(Xh_flat, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                Qh_flat.copy_(bufs[1][3], non_blocking=True)
+            for st_ in (s_in, s_out):
+                stream.wait_stream(st_)
+
+        def both_timed():
+            for st_ in (s_in, s_out):
+                st_.wait_stream(stream)
+            both()
+        ms_both = timed(both_timed, 3, 1)
+        e2e_timeline = {"period_ms": round(period, 3),
+                        "upload_ms": round(statistics.median(b - a for a, b in (t["up"] for t in tl)), 3),
+                        "factor_ms": round(statistics.median(b - a for a, b in (t["run"] for t in tl)), 3),
+                        "download_ms": round(statistics.median(b - a for a, b in (t["down"] for t in tl)), 3),
+                        "h2d_and_d2h_together_ms": round(ms_both, 3),
+                        "steps": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in t.items()} for t in tl]}
+        e2e = {"value": round(world * m * N * 4 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": m * N * 4, "d2h_bytes_per_step": m * N * 4 + N * N * 8,
+               "ms_per_step": round(ms_e2e, 3), "h2d_ms": round(ms_h2d, 3), "d2h_ms": round(ms_d2h, 3),
+               "buffer_sets": NSETS, "timeline": e2e_timeline}
+        del bufs, Xh_flat, Qh_flat
+        torch.cuda.empty_cache()
 
     # measured arithmetic roofs (throughput probes, each launch timed alone)
     scratch = torch.empty(int(rc.lib.rcqr_probe_scratch_bytes()), dtype=torch.uint8, device=dev)
@@ -481,7 +494,8 @@ def run_ours(args):
     del scratch
 
     variants = None
-    if not args.no_variants and m == M:
+    headline = (m, N, K) == (M, 64, 256)
+    if not args.no_variants and headline:
         variants = measure_variants(rc, inputs, timed, dev, X32, ws32, Q32)
 
     peaks = {}
@@ -497,18 +511,20 @@ def run_ours(args):
     # with the largest share of the step
     def roof(name, kernel, nbytes, ms):
         ach = nbytes / (ms * 1e-3) / 1e9
-        tr = TRAFFIC.get(name) if m == M else None
+        tr = TRAFFIC.get(name) if (m, N, K) == (M, 64, 256) else None
         return {"kernel": kernel, "bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "traffic": tr, "peak_source": peak_src,
                 "algorithmic_bytes": nbytes, "ms": round(ms, 4)}
     roofs = {
         "sketch": roof("sketch", "rcqr_sketch: block_exp_kernel + sketch_tc_kernel + reduction (FP32 X)",
                        m * N * 4, ms_sketch),
-        "trsm_gram": roof("trsm_gram", "rcqr_trsm_gram: trsm_tc_kernel<GRAM> (blocked substitution on tcgen05 "
-                          "fused with A = Q^T Q) + prep + Gram reduction (FP32 X)", m * N * 8, ms_tg),
-        "trsm": roof("trsm", "rcqr_trsm: trsm_tc_kernel (blocked substitution on tcgen05) + prep (FP32 X -> Q)",
-                     m * N * 8, ms_trsm),
+        "trsm": roof("trsm", "rcqr_trsm: trsm32 SIMT substitution + prep (FP32 X -> Q)", m * N * 8, ms_trsm),
     }
+    if ms_tg is not None:
+        roofs["trsm_gram"] = roof("trsm_gram", ("rcqr_trsm_gram: trsm_tc_kernel (blocked substitution on tcgen05 "
+                                                "fused with A = Q^T Q)" if 32 < N <= 64 else
+                                                "rcqr_trsm_gram: trsm32_gram_kernel") +
+                                  " + prep + Gram reduction (FP32 X)", m * N * 8, ms_tg)
     dominant = max(roofs, key=lambda k_: roofs[k_]["ms"])
     # the sketch against its generation roof: k Theta entries per X row, 16 entries per
     # Philox call for the Gaussian levels (measured Philox calls/s x 16 entries/call)
@@ -538,7 +554,8 @@ def run_ours(args):
             "accuracy": {"orth_QtQ_minus_I": orth32, "residual_rel_F": res32, "status_ok": ok32},
             "fp64_path": fp64,
             "variants": variants,
-            "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4), "trsm_gram": round(ms_tg, 4)},
+            "kernels_ms": {"sketch": round(ms_sketch, 4), "trsm": round(ms_trsm, 4),
+                           "trsm_gram": round(ms_tg, 4) if ms_tg is not None else None},
             "roofline": roofs[dominant],
             "rooflines": roofs,
             "roofline_sketch_generation": roof_gen,
@@ -546,10 +563,7 @@ def run_ours(args):
                                "fp32_fma_per_s": round(probes["ffma"], 1), "fp64_fma_per_s": round(probes["dfma"], 1),
                                "int32_mad_per_s": round(probes["imad"], 1)},
             "clocks": clocks,
-            "e2e": {"value": round(world * bytes32 / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
-                    "h2d_bytes_per_step": bytes32, "d2h_bytes_per_step": m * N * 4 + N * N * 8,
-                    "ms_per_step": round(ms_e2e, 3), "h2d_ms": round(ms_h2d, 3), "d2h_ms": round(ms_d2h, 3),
-                    "buffer_sets": NSETS, "timeline": e2e_timeline},
+            "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
         }
@@ -560,7 +574,9 @@ def run_ours(args):
 
 
 def main():
+    global N, K
     args = parse()
+    N, K = args.n, args.k
     if args.impl == "reference":
         run_reference(args)
     else:
