@@ -271,7 +271,7 @@ rcqr_status rcqr_implicit_qt_times(const void *Q1, int64_t m, int64_t n, int64_t
                                    int64_t ldrp, const void *B, int64_t ldb, int64_t c, double *Z, int64_t ldz,
                                    void *workspace, size_t ws_bytes, cudaStream_t stream);
 
-/* Column-oriented RCholeskyQR, Alg. 4 (Sec. 3.3), one block of columns per call, for X
+/* Column-oriented RCholeskyQR, Alg. 4 (Sec. 3.2), one block of columns per call, for X
  * whose columns arrive in blocks (e.g. a Krylov basis built from the previous Q):
  * block i is the m x b matrix Xi, holding columns i0 .. i0+b-1 of X; Q (m x n, Q's
  * type by prec), S (k x n double) and R (n x n double) hold the earlier blocks' results

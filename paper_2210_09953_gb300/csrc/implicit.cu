@@ -1,7 +1,7 @@
 // The implicit Q factor of RCholeskyQR2 (the remark after Alg. 3): step 4,
 // Q <- Q1 R'^{-1}, is skipped; Q is kept as the pair (Q1, R') and applied through
 // its products, Q Y = Q1 (R'^{-1} Y) and Q^T B = R'^{-T} (Q1^T B).  Both are
-// stable because Q1 and R' are well conditioned (Sec. 3.2).
+// stable because Q1 and R' are well conditioned (Sec. 3.1).
 //
 // * q_times: W = R'^{-1} Y (n x c, FP64 back substitution, one thread per column),
 //   then Z = Q1 W with one thread per row of Q1 and W in shared memory (in Q1's

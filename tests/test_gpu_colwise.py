@@ -5,7 +5,7 @@ Tolerances: FP64 X, per column relative max(1e-12, 10 n u kappa) for R, S and Q 
 error of the method; blocks are independent least-squares + QR steps in FP64 on both sides).
 FP32 X: ||X - QR|| <= 10 n u32 ||X||, R as the mixed RCholeskyQR tests (the sketch is exact
 to 1e-11, the small steps are FP64).  The block-by-block call (rcqr_colblock_step) on blocks
-generated from the previous Q (the Krylov use of Sec. 3.3) matches the oracle run afterwards
+generated from the previous Q (the Krylov use of Sec. 3.2 and Sec. 6.2) matches the oracle run afterwards
 on the generated X.
 """
 import math
