@@ -214,22 +214,19 @@ rcqr_status run_batch_rr(const rcqr_problem *probs, int count, int variant, int 
     double *Rp = w.take<double>((size_t)p.n * p.n);
     if (!A || !Rp) return RCQR_EWORKSPACE;
     const size_t mark = w.used;
-    auto scratch = [&]() -> Workspace & {
-      w.used = mark;
-      return w;
-    };
     cudaError_t e;
     const bool fused = pass2 && prec != RCQR_F64 && trsm32_gram_supported(p.n);
     if (fused)
       e = launch_trsm32_gram(p.X, p.m, p.n, p.ldx, prec, p.R, p.ldr, p.perm, p.rank, (float *)p.Q, p.ldq, A, p.n,
-                             scratch(), st);
+                             w.rewind(mark), st);
     else
-      e = launch_trsm(p.X, p.m, p.n, p.ldx, prec, p.R, p.ldr, p.perm, p.rank, p.Q, p.ldq, scratch(), st, p.dev_status);
+      e = launch_trsm(p.X, p.m, p.n, p.ldx, prec, p.R, p.ldr, p.perm, p.rank, p.Q, p.ldq, w.rewind(mark), st,
+                      p.dev_status);
     if (e != cudaSuccess) return RCQR_ECUDA;
     if (pass2) {
-      if (!fused && launch_gram(p.Q, p.m, p.n, p.ldq, qprec, p.rank, A, p.n, scratch(), st) != cudaSuccess)
+      if (!fused && launch_gram(p.Q, p.m, p.n, p.ldq, qprec, p.rank, A, p.n, w.rewind(mark), st) != cudaSuccess)
         return RCQR_ECUDA;
-      if (launch_cholqr_pass(A, p.n, p.rank, Rp, p.R, p.ldr, p.Q, p.m, p.ldq, qprec, scratch(), st,
+      if (launch_cholqr_pass(A, p.n, p.rank, Rp, p.R, p.ldr, p.Q, p.m, p.ldq, qprec, w.rewind(mark), st,
                              p.dev_status) != cudaSuccess)
         return RCQR_ECUDA;
     }

@@ -34,6 +34,11 @@ struct Workspace {
     return reinterpret_cast<T *>(base + off);
   }
   bool ok() const { return base != nullptr && used <= cap; }
+  // the same buffer with everything carved after `mark` released again
+  Workspace &rewind(size_t mark) {
+    used = mark;
+    return *this;
+  }
 };
 
 int num_sms();

@@ -35,9 +35,11 @@
 //     (M = 128, K = 16; the exact slices of a group stacked along N, up to 256),
 //     committing them to the stage's "empty" barrier and, after a block's last
 //     stage, to the "accumulators full" barrier;
-//   * warps 12..15 (one per TMEM lane quadrant) fold TMEM into the int64
-//     accumulators (kept in the workspace, L2-resident) once a block's MMAs
-//     are done; the producers never wait for a fold, only for ring slots.
+//   * once a block's MMAs are done, all 16 warps fold TMEM into the int64
+//     accumulators (kept in the workspace, L2-resident), four warps per TMEM
+//     lane quadrant: warps 12..14 do nothing else, warp 15 after issuing the
+//     block's last MMAs, the producers after filling the ring with the next
+//     block's first stages (they would wait for a free slot otherwise).
 // Every wait is bounded; a timeout marks the partial sums NaN and raises
 // RCQR_ETIMEOUT in the status word.
 #include <algorithm>
@@ -54,9 +56,8 @@ namespace rcqr {
 namespace {
 
 constexpr int kThreadsTC = 512;                     // 16 warps
-constexpr int kProdWarps = 12;                      // warps 0..11 produce (Theta, then X); they arrive on "full"
-constexpr int kFoldWarp0 = 12;                      // warps 12..15 fold TMEM (one per lane quadrant);
-                                                    // warp 15 also issues the MMAs
+constexpr int kProdWarps = 12;                      // warps 0..11 produce (Theta, then X); they arrive on "full";
+                                                    // 12..14 only fold; 15 issues the MMAs (all 16 fold)
 // Rows per exponent block / TMEM promotion: products T d stay below 2^13
 // (FP32/BF16: |d| <= 64) or 2^14 (FP64: 7-bit digits), so the fp32 sums are
 // exact over 2048 or 1024 rows.
@@ -141,6 +142,19 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// rint(t) as int64 for an FP32 t with |t| < 2^45, without a 64-bit conversion (those
+// run on the FP64 unit, a small fraction of the FP32 rate): t = h 2^24 + l with h the
+// nearest integer to t 2^-24 (the 1.5 2^23 addition rounds it; |h| < 2^21) and
+// l = t - h 2^24 exact (|l| <= 2^23, a multiple of t's ulp), then rint(l) by one 32-bit
+// conversion.  Equal to __float2ll_rn(t): for |t| >= 2^23, t and l are integers; below,
+// h = 0 and l = t.
+__device__ __forceinline__ long long rint_to_ll(float t) {
+  const float hm = fmaf(t, 0x1p-24f, 0x1.8p23f);
+  const int h = __float_as_int(hm) - 0x4B400000;
+  const float l = fmaf(-(hm - 0x1.8p23f), 0x1p24f, t);
+  return ((long long)h << 24) + __float2int_rn(l);
+}
 
 // Packed pairs (add.rn.f32x2 / mul.rn.f32x2 of the sm_100 family): two
 // independent IEEE round-to-nearest operations in one instruction.
@@ -393,6 +407,7 @@ __device__ __forceinline__ void wait_or_fail(uint64_t *bar, uint32_t parity, int
   *f = 1;
 }
 
+
 template <int PREC, int KCH, int JCH>
 struct Tc {
   using Cfg = SliceCfg<PREC>;
@@ -423,20 +438,17 @@ struct Tc {
     int e_blk[NC];       // the folded block's column exponents
   };
 
-  // Folds block b's TMEM accumulators into the int64 accumulators.  Run by the
-  // four fold warps (warp w reads TMEM lanes 32 (w % 4) ..); each thread owns one
-  // Theta row of every chunk and all NC columns.  Ends with a barrier of the
-  // fold warps, after which TMEM may be overwritten.
+  // Folds block b's TMEM accumulators into the int64 accumulators.  Run by all
+  // 16 warps of the CTA (the producers join once they have filled the ring with
+  // the next block's first stages, so the fold is off no one's critical path but
+  // the MMA thread's): warp w reads TMEM lanes 32 (w % 4) .. (its lane quadrant)
+  // and takes every fourth 8-column chunk, starting at chunk w / 4; each thread
+  // owns one Theta row of its chunks.  Starts and ends with a barrier of the
+  // whole CTA, after which TMEM may be overwritten.
   static __device__ __noinline__ void fold(Shared &sh, int b, int NB, uint32_t tbase, long long *Acc,
                                            const TcArgs &a, int kgi, int col0, int g, int64_t blk) {
-    const int ft = threadIdx.x - 32 * kFoldWarp0, lane = threadIdx.x & 31, lq = (threadIdx.x >> 5) & 3;
-    const int *eb = a.eblk + (blk - a.blk0) * a.n;
-    for (int jl = ft; jl < NC; jl += 128) sh.e_blk[jl] = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
-    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256, a.polls);
-    umma::fence_after_sync();
-    umma::named_sync(128);
-    const bool last = b == NB - 1;
-    const int p = b & 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lq = warp & 3, part = warp >> 2;
     const int il = 32 * lq + lane;
     // chunks of 8 columns; this thread's 8 accumulators of a chunk are contiguous,
     // Acc[(c 128 + il) NC + jl], and the next chunk's are loaded while this one is folded
@@ -445,20 +457,27 @@ struct Tc {
       return reinterpret_cast<longlong2 *>(Acc + ((size_t)(ch / CPC) * 128 + il) * NC + (ch % CPC) * 8);
     };
     longlong2 nxt[4];
-    if (b > 0) {
+    if (b > 0 && part < NCH) {
 #pragma unroll
-      for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(0)[h];
+      for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(part)[h];
     }
+    const int *eb = a.eblk + (blk - a.blk0) * a.n;
+    for (int jl = tid; jl < NC; jl += kThreadsTC) sh.e_blk[jl] = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
+    wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256, a.polls);
+    umma::fence_after_sync();
+    umma::named_sync(kThreadsTC);
+    const bool last = b == NB - 1;
+    const int p = b & 1;
 #pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
+    for (int ch = part; ch < NCH; ch += 4) {
       const int c = ch / CPC, jc0 = (ch % CPC) * 8;
       const int i = (kgi * KCH + c) * 128 + il;
       longlong2 old2[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) old2[h] = nxt[h];
-      if (b > 0 && ch + 1 < NCH) {
+      if (b > 0 && ch + 4 < NCH) {
 #pragma unroll
-        for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(ch + 1)[h];
+        for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(ch + 4)[h];
       }
       uint32_t rv[NACC][8];
 #pragma unroll
@@ -482,7 +501,7 @@ struct Tc {
 #pragma unroll
           for (int bs = 0; bs < NE; ++bs)
             V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
-          V += __float2ll_rn(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));
+          V += rint_to_ll(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));   // |.| < 2^35
           const int f = e - TOP - 7 * NE - LS;
           if (Ec == EMPTY_EXP) {
             acc_v = V;
@@ -511,7 +530,7 @@ struct Tc {
       }
     }
     // running exponents after this block
-    for (int jl = ft; jl < NC; jl += 128) {
+    for (int jl = tid; jl < NC; jl += kThreadsTC) {
       const int e = sh.e_blk[jl];
       const int Ec = sh.E_col[p][jl];
       int En = Ec;
@@ -522,7 +541,7 @@ struct Tc {
       sh.E_col[p ^ 1][jl] = En;
     }
     umma::fence_before_sync();
-    umma::named_sync(128);
+    umma::named_sync(kThreadsTC);
   }
 };
 
@@ -646,8 +665,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     else calls.init(tid, kgi);
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
       const int b = it / kSPB, st = it % kSPB;
+      // the ring holds the next block's first D stages: fold the previous block (the
+      // next slot is released only by MMAs issued after that fold)
+      if (st == D && b > 0) K::fold(sh, b - 1, NB, tbase, Acc, a, kgi, col0, g, bb + b - 1);
+      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
       const int64_t r0 = (bb + b) * kBlockRows + st * kBK;
       if (rademacher) rad.tile(stage_base + slot * K::STAGE_BYTES, r0, a);
       else calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, r0, a);
@@ -655,6 +677,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
     }
+    if (NB > 0) K::fold(sh, NB - 1, NB, tbase, Acc, a, kgi, col0, g, bb + NB - 1);
   } else if (warp < kProdWarps) {
     // ---- X producers: task o = xt + NXT u is column jl = 8 (o / 32) + o % 8, octet oc = (o / 8) % 4
     // (8 consecutive lanes: 8 consecutive columns of one octet, so the slice stores do not conflict)
@@ -694,6 +717,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     for (int it = 0; it < total; ++it) {
       const int slot = it % D;
       const int b = it / kSPB, st = it % kSPB;
+      if (st == D && b > 0) K::fold(sh, b - 1, NB, tbase, Acc, a, kgi, col0, g, bb + b - 1);
       if (it + kXAhead < total)
 #pragma unroll
         for (int u = 0; u < TPT; ++u) issue(it + kXAhead, (it + kXAhead) % kXSlots, xt + NXT * u);
@@ -730,11 +754,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
     }
     cp_async_wait<0>();
+    if (NB > 0) K::fold(sh, NB - 1, NB, tbase, Acc, a, kgi, col0, g, bb + NB - 1);
   } else if (warp < kThreadsTC / 32 - 1) {
-    // ---- fold warps 12..14
+    // ---- warps 12..14: fold only
     for (int b = 0; b < NB; ++b) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g, bb + b);
   } else {
-    // ---- warp 15: one thread issues the MMAs; after a block's last stage the warp folds with warps 12..14.
+    // ---- warp 15: one thread issues the MMAs; after a block's last stage the warp folds with the others.
     // Slices 0..NE feed consecutive accumulators and sit consecutively in the
     // stage, so up to 256 / NC of them form one MMA with N = (count) NC (the
     // Theta tile is then read once for all of them); the slices below NE add
@@ -841,10 +866,17 @@ TcPlan plan_tc(int64_t m, int64_t n, int64_t k, int64_t row_offset, int prec) {
   p.BR = block_rows(prec);
   p.blk0 = row_offset / p.BR;
   p.nblk = (row_offset + m + p.BR - 1) / p.BR - p.blk0;
+  // row groups: one wave of CTAs (one per SM) when every CTA can take its share of
+  // the blocks (at most maxb, the int64 headroom); otherwise as many groups as fill
+  // whole waves, so the last wave is not a partial one
   const int64_t ctas_per_rows = (int64_t)p.kgrp * p.ngrp;
-  int64_t groups = std::max<int64_t>(1, num_sms() / ctas_per_rows);
-  groups = std::min<int64_t>(groups, p.nblk);
-  groups = std::max<int64_t>(groups, (p.nblk + maxb - 1) / maxb);
+  const int64_t sms = num_sms();
+  const int64_t gmin = (p.nblk + maxb - 1) / maxb;
+  int64_t groups = std::min<int64_t>(std::max<int64_t>(1, sms / ctas_per_rows), p.nblk);
+  if (groups < gmin) {
+    const int64_t waves = (gmin * ctas_per_rows + sms - 1) / sms;
+    groups = std::min<int64_t>(std::max<int64_t>(gmin, waves * sms / ctas_per_rows), p.nblk);
+  }
   p.groups = (int)std::min<int64_t>(groups, 65535);
   return p;
 }
