@@ -136,6 +136,12 @@ cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, 
                                int *dev_status);
 
 // W = R^{-1} (n x n upper) for the leading rank x rank block (rank nullable).
+// Q <- Q R'^{-1} for FP32 Q, 16 < n <= 128: W = R'^{-1} in FP64, then Q W on the tensor
+// cores with an exact leading term (gemm_tc.cu); workspace gemm_tc_workspace(n).
+bool gemm_tc_supported(int64_t n);
+size_t gemm_tc_workspace(int64_t n);
+cudaError_t launch_inverse_times(float *Q, int64_t m, int64_t n, int64_t ldq, const double *Rp, int64_t ldrp,
+                                 const int64_t *rank, int *status, Workspace &ws, cudaStream_t st);
 cudaError_t launch_tri_inverse(const double *R, int64_t n, int64_t ldr, const int64_t *rank,
                                double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_reset_status(int *dev_status, cudaStream_t st);

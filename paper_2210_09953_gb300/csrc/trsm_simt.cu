@@ -129,7 +129,9 @@ int gram_groups(int64_t m, int64_t n) {
 
 size_t trsm_workspace(int64_t m, int64_t n, int prec) {
   (void)m;
-  return (prec != RCQR_F64 && trsm32_supported(n)) ? trsm32_workspace(n) : 0;
+  if (prec == RCQR_F64) return 0;
+  const size_t t = trsm32_supported(n) ? trsm32_workspace(n) : 0;
+  return gemm_tc_supported(n) ? std::max(t, gemm_tc_workspace(n)) : t;
 }
 
 // FP64 X: row-wise substitution in FP64 (here).  FP32 / BF16 X: the FP32
@@ -160,6 +162,10 @@ cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, 
                                int *dev_status) {
   cudaError_t e = launch_chol_update(A, n, n, rank, Rp, n, R, ldr, dev_status, st);
   if (e != cudaSuccess) return e;
+  // FP32 Q: Q R'^{-1} as a tensor-core product with the explicit inverse (R' is well
+  // conditioned; gemm_tc.cu); FP64 Q: the FP64 substitution
+  if (qprec == RCQR_F32 && gemm_tc_supported(n))
+    return launch_inverse_times((float *)Q, m, n, ldq, Rp, n, rank, dev_status, ws, st);
   return launch_trsm(Q, m, n, ldq, qprec, Rp, n, nullptr, rank, Q, ldq, ws, st, dev_status);
 }
 

@@ -13,7 +13,8 @@
   (oracle.rcqr.rcholqr_f32: sketch and QR in FP64, substitution in float32), and
   sigma(Q) inside the Thm. 5.2 interval (with the exact eps of the drawn Theta and u =
   2^-24) wherever that interval is not vacuous.
-* Alg. 3 on the mixed path: ||Q^T Q - I|| <= 1e-6 at every condition number tested.
+* Alg. 3 on the mixed path: ||Q^T Q - I|| <= 1e-6 at every condition number tested, for
+  n = 64, 100 and 128 (the second pass by the tensor-core product with R'^{-1}).
 * Alg. 5 with FP32 / BF16 X (the sketch exact to SKETCH_TOL, the rest FP64): Z and R
   against the FP64 oracle on the stored X, and Thm. 5.4 (rmain1) for Z against L Q.
 * A zero column of X: R_jj = 0, Q's column j and the Gram of Alg. 3 step 2 are NaN, so
@@ -155,8 +156,9 @@ def test_mixed_rcholqr_conditioning_against_f32_oracle(rc, inputs, prec, cond):
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("cond", [1e4, 1e8, 1e12])
-def test_mixed_rcholqr2_orthogonality(rc, inputs, prec, cond):
-    m, n, k = 30011, 64, 256
+@pytest.mark.parametrize("n", [64, 100, 128])
+def test_mixed_rcholqr2_orthogonality(rc, inputs, prec, cond, n):
+    m, k = 30011, 4 * n
     X = inputs.svd_matrix(m, n, cond, 1401, dtype=prec, device=DEV)
     Q, R, _, _, status = rc.rcqr_factor(X, k, 0x5EED0002, variant=rc.DIRECT2)
     torch.cuda.synchronize()

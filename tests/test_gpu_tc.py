@@ -12,6 +12,8 @@ Tolerances (u = 2^-24, the mixed path's working precision):
 Shapes: a single partial tile (m < 128), exact multiples of the 128-row tile, ragged tails,
 n = 33 (one used column in the last 16-column block), n = 48, 64, a permuted rank-deficient
 call (the rank-revealing form of Alg. 7 step 4) and Q in place of X (Alg. 3 step 4).
+The last test checks the second pass's product with the explicit inverse (bound stated
+there) for 16 < n <= 128.
 """
 import numpy as np
 import pytest
@@ -117,3 +119,34 @@ def test_tc_substitution_in_place(rc, inputs):
     torch.cuda.synchronize()
     assert np.array_equal(host64(Y), Qs)
     check_substitution(Xh, Qs, Ro, n, 10.0)
+
+
+# ----------------------------------------------------------------------------- pass 2 by the explicit inverse
+# Alg. 3 step 4 on the mixed path, Q <- Q1 W with W = R'^{-1} (FP64) as a tensor-core
+# product whose leading term is exact (gemm_tc.cu).  Q1 and R' come from
+# rcqr_factor_implicit, which runs the same kernels as rcqr_factor up to Alg. 3 step 3.
+# Bound, entrywise: every entry of Q1 and of W is represented to 2^-22 of itself (an
+# 8-bit digit and two FP16 pieces after scaling by 2^(14 - e) per row of Q1 / column of
+# W), except that the last piece has an absolute resolution of 2^-24 scaled units
+# (FP16 subnormals), 2^-38 of the row's or column's largest entry; the one product
+# dropped is below 2^-22 of |q||w|, and the result is rounded to FP32 once:
+#   |Q - Q1 W| <= 2^-20 (|Q1| |W|) + 2^-36 (rowsum |Q1| colmax |W| + rowmax |Q1| colsum |W|)
+#                 + 2 u |Q|,  u = 2^-24.
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n,k,cond", [(30011, 64, 256, 1e8), (20000, 100, 400, 1e8), (9001, 128, 512, 1e12),
+                                        (1000, 40, 160, 1e4), (257, 17, 72, 1e6)])
+def test_pass2_product_with_explicit_inverse(rc, inputs, prec, m, n, k, cond):
+    X = inputs.svd_matrix(m, n, cond, 700 + n, dtype=prec, device=DEV)
+    Q1, R1, Rp, st1 = rc.rcqr_factor_implicit(X, k, 31)
+    Q, R, _, _, st2 = rc.rcqr_factor(X, k, 31, variant=rc.DIRECT2)
+    torch.cuda.synchronize()
+    assert int(st1[0]) == 0 and int(st2[0]) == 0
+    Q1h, Rph, Qh = host64(Q1), host64(Rp), host64(Q)
+    W = olin.triangular_inverse(Rph)
+    E = np.abs(Qh - Q1h @ W)
+    aQ, aW = np.abs(Q1h), np.abs(W)
+    tiny = aQ.sum(1, keepdims=True) * aW.max(0, keepdims=True) + aQ.max(1, keepdims=True) * aW.sum(0, keepdims=True)
+    assert np.all(E <= 2.0 ** -20 * (aQ @ aW) + 2.0 ** -36 * tiny + 2 * U32 * np.abs(Qh))
+    from oracle import rcqr as orc
+    assert orc.orthogonality(Qh) <= 1e-6
