@@ -21,6 +21,9 @@
 // entry is represented to 2^-22 of itself and the whole product to about 2^-21 of
 // |Q| |W| entrywise.  The result is (D_hh + D_s) 2^(e_t - 14) 2^(e_j - 14), rounded once.
 //
+// The Gram matrix A = Q^T Q of the first pass's Q (Alg. 3 step 2), 64 < n <= 128, uses
+// the same pieces with the scales per tile and column (gram_tc_kernel below).
+//
 // Layout.  A CTA takes tiles of 128 rows (TMEM lane t = row t); NP = 64 or 128 padded
 // columns.  The row pieces h | m | l form one K-major operand of K extent 3 NP (thread
 // t writes its row's 8-column chunks as 16-byte core-matrix rows).  W is upper
@@ -255,6 +258,186 @@ __global__ void __launch_bounds__(GemmCfg<NP>::THREADS, GemmCfg<NP>::CTAS) gemm_
   if (warp == 0) umma::tmem_dealloc(tbase, C::NCOLS);
 }
 
+// ---------------------------------------------------------------------------------
+// A = Q^T Q for 64 < n <= 128 (NP = 128), FP32 Q.  A CTA of 512 threads takes tiles of
+// 128 rows; thread (r, g) holds row r of the tile and columns 32 g .. 32 g + 31, and in
+// the fold it owns row i = r of A at the same columns (TMEM lane i, warp w reading lanes
+// 32 (w % 4) ..).  Per tile and column j, the column is scaled by 2^(14 - e_j) (e_j from
+// the tile's largest |q|) and split into h (8-bit digit times 256), m, l as FP16, K-major
+// along the columns like gemm_tc_kernel's row pieces, which the tensor cores read as the
+// transposed (MN-major) operands.  Every h_ri h_rj is an integer below 2^14 times 2^16,
+// so D_hh = H^T H over the 128 rows is exact; H^T M (8 accumulations, at most 2^-7 of
+// the leading term), H^T L and M^T M go to accumulators of their own.  After every tile
+// each thread adds
+//     (h h / 2 + h m + h l + m m / 2) 2^(e_i - 14) 2^(e_j - 14)
+// for its 32 entries into FP32 Kahan sums S; the CTA's partial is S in FP64, and the
+// reduction forms A = sum over CTAs of (S + S^T) (the dropped m l, l m, l l are below
+// 2^-26 of |q_i||q_j|).
+constexpr int kGramThreads = 512;
+constexpr int kGramCols = 32;                 // columns per thread
+constexpr int kGramNP = 128;
+constexpr uint32_t kGramYSBO = (3 * kGramNP / 8) * 128;
+constexpr int kGramY = kGR * 3 * kGramNP * 2;  // 96 KB of pieces
+constexpr int kGramSmem = kGramY + 4 * kGramNP * 4 + 2 * kGramNP * 4;   // + warp maxima + scale pairs
+
+__global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *__restrict__ Q, int64_t m, int n,
+                                                                 int64_t ldq, double *partial, int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *Ys = smem;
+  unsigned *Wmax = reinterpret_cast<unsigned *>(smem + kGramY);         // 4 x NP: per warp row group
+  float *Sc = reinterpret_cast<float *>(smem + kGramY + 4 * kGramNP * 4), *Isc = Sc + kGramNP;
+  __shared__ uint64_t bar_mma, bar_drain;
+  __shared__ uint32_t tslot;
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int trow = tid % kGR, grp = tid / kGR;          // row of the tile, column group
+  const int c0 = kGramCols * grp;
+  if (tid == 0) {
+    umma::mbar_init(&bar_mma, 1);
+    umma::mbar_init(&bar_drain, 1);
+    s_fail = 0;
+  }
+  if (warp == 0) umma::tmem_alloc(&tslot, 512u);        // D_hh | D_hm | D_hl | D_mm, 128 columns each
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tbase = tslot;
+  const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t ys_addr = umma::smem_u32(Ys);
+  const uint32_t row_sw = (uint32_t)(trow / 8) * kGramYSBO + (uint32_t)(trow % 8) * 16;
+  float acc[kGramCols], cmp[kGramCols];
+#pragma unroll
+  for (int c = 0; c < kGramCols; ++c) acc[c] = cmp[c] = 0.0f;
+  uint32_t ph = 0;
+
+  const int64_t tiles = (m + kGR - 1) / kGR;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * kGR + trow;
+    const bool live = row < m;
+    float y[kGramCols];
+#pragma unroll
+    for (int c = 0; c < kGramCols; ++c) {
+      const int j = c0 + c;
+      y[c] = (live && j < n) ? Q[row + (int64_t)j * ldq] : 0.0f;
+    }
+    // per column, the tile's largest |q|: warp maxima, then the four row groups
+#pragma unroll
+    for (int c = 0; c < kGramCols; ++c) {
+      const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(y[c]) & 0x7FFFFFFFu);
+      if (lane == 0) Wmax[(warp & 3) * kGramNP + c0 + c] = mx;
+    }
+    __syncthreads();
+    if (tid < kGramNP) {
+      const unsigned mx = max(max(Wmax[tid], Wmax[kGramNP + tid]), max(Wmax[2 * kGramNP + tid], Wmax[3 * kGramNP + tid]));
+      fixed_scales((int)(mx >> 23), Sc[tid], Isc[tid]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c8 = 0; c8 < kGramCols / 8; ++c8) {
+      uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int c = 8 * c8 + 2 * p;
+        split_row2(y[c] * Sc[c0 + c], y[c + 1] * Sc[c0 + c + 1], hw[p], mw[p], lw[p]);
+      }
+      const int col = c0 + 8 * c8;
+      *reinterpret_cast<uint4 *>(Ys + row_sw + ((0 * kGramNP + col) / 8) * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(Ys + row_sw + ((1 * kGramNP + col) / 8) * 128) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+      *reinterpret_cast<uint4 *>(Ys + row_sw + ((2 * kGramNP + col) / 8) * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && !*(volatile int *)&s_fail) {
+      umma::fence_after_sync();
+      // MN-major views of the pieces: 8-column groups 128 B apart (SBO), 8-row groups
+      // kGramYSBO apart (LBO); (A piece, B piece, accumulator)
+      const uint32_t id = umma::idesc_f16_f32(kGR, kGramNP) | (1u << 15) | (1u << 16);
+      const int pa[4] = {0, 0, 0, 1}, pb[4] = {0, 1, 2, 1};
+#pragma unroll
+      for (int t = 0; t < kGR / 16; ++t) {
+        const uint32_t kofs = (uint32_t)(2 * t) * kGramYSBO;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const uint64_t ad = umma::smem_desc(ys_addr + kofs + ((pa[p] * kGramNP) / 8) * 128, kGramYSBO, 128);
+          const uint64_t bd = umma::smem_desc(ys_addr + kofs + ((pb[p] * kGramNP) / 8) * 128, kGramYSBO, 128);
+          umma::mma_bf16(tbase + (uint32_t)(p * kGramNP), ad, bd, id, t > 0 ? 1u : 0u);
+        }
+      }
+      umma::mma_commit(&bar_mma);
+    }
+    wait_mma(&bar_mma, ph, &s_fail);
+    ph ^= 1u;
+    umma::fence_after_sync();
+    // fold: row i = trow of this tile's A, columns c0 ..
+    const float isi = Isc[trow];
+#pragma unroll
+    for (int c8 = 0; c8 < kGramCols / 8; ++c8) {
+      uint32_t vhh[8], vhm[8], vhl[8], vmm[8];
+      const uint32_t col = (uint32_t)(c0 + 8 * c8);
+      umma::tmem_ld8(lane_base + col, vhh);
+      umma::tmem_ld8(lane_base + kGramNP + col, vhm);
+      umma::tmem_ld8(lane_base + 2 * kGramNP + col, vhl);
+      umma::tmem_ld8(lane_base + 3 * kGramNP + col, vmm);
+      umma::tmem_wait_ld();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = 8 * c8 + u;
+        const float t = (0.5f * (__uint_as_float(vhh[u]) + __uint_as_float(vmm[u])) + __uint_as_float(vhm[u]) +
+                         __uint_as_float(vhl[u])) * (isi * Isc[c0 + c]);
+        const float yk = t - cmp[c];
+        const float sk = acc[c] + yk;
+        cmp[c] = (sk - acc[c]) - yk;
+        acc[c] = sk;
+      }
+    }
+    umma::fence_before_sync();
+    __syncthreads();   // TMEM, the pieces and the scales are free for the next tile
+  }
+  // the CTA's partial S (row i = trow, this thread's columns), in FP64
+  const bool failed = *(volatile int *)&s_fail != 0;
+  if (trow < n) {
+    double *pb = partial + (int64_t)blockIdx.x * n * n;
+#pragma unroll
+    for (int c = 0; c < kGramCols; ++c) {
+      const int j = c0 + c;
+      if (j < n) pb[trow + (int64_t)j * n] = failed ? __longlong_as_double(0x7FF8000000000000ll)
+                                                    : (double)acc[c] - (double)cmp[c];
+    }
+  }
+  if (tid == 0) {
+    umma::mma_commit(&bar_drain);
+    if (!umma::mbar_wait(&bar_drain, 0u, 1u << 22)) s_fail = 1;
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && *(volatile int *)&s_fail && status && atomicCAS(status, 0, (int)RCQR_ETIMEOUT) == 0) status[1] = -1;
+  if (warp == 0) umma::tmem_dealloc(tbase, 512u);
+}
+
+// A(i, j) = sum over the CTAs g of S_g(i, j) + S_g(j, i), in a fixed order (one warp per entry).
+__global__ void gram_sym_reduce_kernel(const double *__restrict__ partial, int groups, int n, double *__restrict__ A,
+                                       int64_t lda) {
+  const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int g = lane; g < groups; g += 32) {
+    const double *pg = partial + (int64_t)g * n * n;
+    s += pg[i + (int64_t)j * n] + pg[j + (int64_t)i * n];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) A[i + (int64_t)j * lda] = s;
+}
+
+int gram_tc_groups(int64_t m) {
+  const int64_t tiles = (m + kGR - 1) / kGR;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms()));
+}
+
 // W = R'^{-1} on the leading r x r block (zero elsewhere), then W's pieces for
 // gemm_tc_kernel: one warp per column c of the padded NP columns.  Back substitution
 // w_i = -(sum_{l = i+1..c} R'_il w_l) / R'_ii (w_c = 1 / R'_cc), the sum split over the
@@ -339,6 +522,27 @@ cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st) {
 }  // namespace
 
 bool gemm_tc_supported(int64_t n) { return n > 64 && n <= 128; }
+
+bool gram_tc_supported(int64_t n) { return n > 64 && n <= 128; }
+
+size_t gram_tc_workspace(int64_t m, int64_t n) {
+  Workspace w(nullptr, 0);
+  w.take<double>((size_t)gram_tc_groups(m) * n * n);
+  return w.used;
+}
+
+cudaError_t launch_gram_tc(const float *Q, int64_t m, int64_t n, int64_t ldq, double *A, int64_t lda, int *status,
+                           Workspace &ws, cudaStream_t st) {
+  const int G = gram_tc_groups(m);
+  double *partial = ws.take<double>((size_t)G * n * n);
+  if (!partial) return cudaErrorMemoryAllocation;
+  cudaError_t e = set_smem(gram_tc_kernel, kGramSmem);
+  if (e != cudaSuccess) return e;
+  gram_tc_kernel<<<G, kGramThreads, kGramSmem, st>>>(Q, m, (int)n, ldq, partial, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gram_sym_reduce_kernel<<<(unsigned)((n * n * 32 + 255) / 256), 256, 0, st>>>(partial, G, (int)n, A, lda);
+  return cudaGetLastError();
+}
 
 size_t gemm_tc_workspace(int64_t n) {
   Workspace w(nullptr, 0);

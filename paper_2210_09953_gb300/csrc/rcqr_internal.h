@@ -142,6 +142,12 @@ bool gemm_tc_supported(int64_t n);
 size_t gemm_tc_workspace(int64_t n);
 cudaError_t launch_inverse_times(float *Q, int64_t m, int64_t n, int64_t ldq, const double *Rp, int64_t ldrp,
                                  const int64_t *rank, int *status, Workspace &ws, cudaStream_t st);
+// A = Q^T Q for FP32 Q, 64 < n <= 128, on the tensor cores (gemm_tc.cu); workspace
+// gram_tc_workspace(m, n).
+bool gram_tc_supported(int64_t n);
+size_t gram_tc_workspace(int64_t m, int64_t n);
+cudaError_t launch_gram_tc(const float *Q, int64_t m, int64_t n, int64_t ldq, double *A, int64_t lda, int *status,
+                           Workspace &ws, cudaStream_t st);
 cudaError_t launch_tri_inverse(const double *R, int64_t n, int64_t ldr, const int64_t *rank,
                                double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_reset_status(int *dev_status, cudaStream_t st);

@@ -172,12 +172,15 @@ cudaError_t launch_cholqr_pass(const double *A, int64_t n, const int64_t *rank, 
 size_t gram_workspace(int64_t m, int64_t n) {
   Workspace w(nullptr, 0);
   w.take<double>((size_t)std::max(gram_groups(m, n), gram32_groups(m, n)) * n * n);
+  if (gram_tc_supported(n)) return std::max(w.used, gram_tc_workspace(m, n));
   return w.used;
 }
 
 cudaError_t launch_gram(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec,
                         const int64_t *rank, double *A, int64_t lda, Workspace &ws,
                         cudaStream_t st) {
+  if (prec != RCQR_F64 && gram_tc_supported(n))
+    return launch_gram_tc((const float *)Q, m, n, ldq, A, lda, nullptr, ws, st);   // NaN A on a timeout
   if (prec != RCQR_F64) {
     const int g32 = gram32_groups(m, n);
     double *p32 = ws.take<double>((size_t)g32 * n * n);

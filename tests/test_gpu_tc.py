@@ -150,3 +150,27 @@ def test_pass2_product_with_explicit_inverse(rc, inputs, prec, m, n, k, cond):
     assert np.all(E <= 2.0 ** -20 * (aQ @ aW) + 2.0 ** -36 * tiny + 2 * U32 * np.abs(Qh))
     from oracle import rcqr as orc
     assert orc.orthogonality(Qh) <= 1e-6
+
+
+# ----------------------------------------------------------------------------- tensor-core Gram, 64 < n <= 128
+# A = Q^T Q (Alg. 3 step 2) on the tensor cores (gemm_tc.cu): per tile and column an 8-bit
+# digit and two FP16 pieces (each entry to 2^-22 of itself), the digit products exact, the
+# next products in FP32 over at most eight 16-row steps (2^-21 of at most 2^-7 of the
+# leading term), per-tile Kahan sums, FP64 across CTAs; the dropped products are below
+# 2^-26.  Bound, entrywise: |A - Q^T Q| <= 2^-19 (|Q|^T |Q|).
+
+@pytest.mark.parametrize("m,n", [(100, 65), (70001, 100), (128 * 300, 128), (9999, 128)])
+def test_gram_tensor_core(rc, inputs, m, n):
+    g = torch.Generator(device="cpu").manual_seed(1000 + n)
+    Qh = torch.randn((m, n), dtype=torch.float64, generator=g).numpy()
+    Qh *= 10.0 ** (np.arange(n) / 25.0)[None, :]                 # columns of different scales
+    Qh[: m // 3] *= 1e-3                                        # and rows of different scales
+    Qh[:, n // 2] = 0.0                                          # one zero column
+    Q32 = Qh.astype(np.float32)
+    Q = torch.from_numpy(Q32).to(DEV).t().contiguous().t()
+    A = host64(rc.rcqr_gram(Q))
+    torch.cuda.synchronize()
+    Qd = Q32.astype(np.float64)
+    Ao = Qd.T @ Qd
+    assert np.array_equal(A, A.T)
+    assert np.all(np.abs(A - Ao) <= 2.0 ** -19 * (np.abs(Qd).T @ np.abs(Qd)))
