@@ -148,6 +148,12 @@ bool gram_tc_supported(int64_t n);
 size_t gram_tc_workspace(int64_t m, int64_t n);
 cudaError_t launch_gram_tc(const float *Q, int64_t m, int64_t n, int64_t ldq, double *A, int64_t lda, int *status,
                            Workspace &ws, cudaStream_t st);
+// Q = X R^{-1} for 64 < n <= 128, FP32 / BF16 X: blocked substitution with the
+// off-diagonal products on the tensor cores (trsm_tcw.cu); Rf, dinv from trsm32_prep_kernel.
+bool trsm_tcw_supported(int64_t n);
+cudaError_t launch_trsm_tcw(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
+                            const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
+                            int *status, cudaStream_t st);
 cudaError_t launch_tri_inverse(const double *R, int64_t n, int64_t ldr, const int64_t *rank,
                                double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_reset_status(int *dev_status, cudaStream_t st);

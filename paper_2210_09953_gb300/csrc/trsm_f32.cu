@@ -553,6 +553,8 @@ cudaError_t launch_trsm32(const void *X, int64_t m, int64_t n, int64_t ldx, int 
   float *dinv = ws.take<float>((size_t)NB);
   if (!Rf || !dinv) return cudaErrorMemoryAllocation;
   trsm32_prep_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rank, NB, Rf, dinv);
+  if (trsm_tcw_supported(n))   // 64 < n <= 128: blocked, off-diagonal products on the tensor cores
+    return launch_trsm_tcw(X, m, n, ldx, prec, Rf, dinv, perm, rank, (float *)Q, ldq, nullptr, st);
   if (n > 64) {
     const unsigned blocks = (unsigned)((m + kT32Threads - 1) / kT32Threads);
     if (prec == RCQR_BF16)

@@ -174,3 +174,42 @@ def test_gram_tensor_core(rc, inputs, m, n):
     Ao = Qd.T @ Qd
     assert np.array_equal(A, A.T)
     assert np.all(np.abs(A - Ao) <= 2.0 ** -19 * (np.abs(Qd).T @ np.abs(Qd)))
+
+
+# ----------------------------------------------------------------------------- blocked substitution, 64 < n <= 128
+# rcqr_trsm for 64 < n <= 128 runs the eight-block tensor-core substitution (trsm_tcw.cu):
+# the same FP32 backward and forward bounds as the 64-column kernel above.
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n,cond", [(77, 65, 1e3), (128 * 97, 128, 1e6), (70001, 100, 1e8), (30000, 120, 1e2)])
+def test_tc_wide_substitution(rc, inputs, prec, m, n, cond):
+    X = inputs.svd_matrix(m, n, cond, 900 + n, dtype=prec, device=DEV)
+    Ro = upper_r(n, cond, 190 + n)
+    R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
+    Q = rc.rcqr_trsm(X, R)
+    torch.cuda.synchronize()
+    check_substitution(host64(X), host64(Q), Ro, n, cond)
+
+
+def test_tc_wide_substitution_permuted_rank_and_in_place(rc, inputs):
+    m, n, r = 20000, 128, 83
+    X = inputs.svd_matrix(m, n, 1e2, 16, dtype="f32", device=DEV)
+    perm_h = np.random.default_rng(2).permutation(n).astype(np.int32)
+    perm = torch.from_numpy(perm_h).to(DEV)
+    rank = torch.tensor([r], dtype=torch.int64, device=DEV)
+    Ro = np.triu(np.random.default_rng(3).standard_normal((n, n))) + 12 * np.eye(n)
+    R = torch.from_numpy(Ro).to(DEV).t().contiguous().t()
+    Q = host64(rc.rcqr_trsm(X, R, perm=perm, rank=rank))
+    torch.cuda.synchronize()
+    Xs = host64(X)[:, perm_h[:r]]
+    R11 = Ro[:r, :r].astype(np.float32).astype(np.float64)
+    check_substitution(Xs, Q[:, :r], R11, r, np.linalg.cond(R11))
+    assert np.all(Q[:, r:] == 0)
+    # Q in place of X (Alg. 3 step 4 form), bit-equal to the out-of-place call
+    Ro2 = upper_r(n, 10.0, 17)
+    R2 = torch.from_numpy(Ro2).to(DEV).t().contiguous().t()
+    Qs = host64(rc.rcqr_trsm(X.clone(), R2))
+    Y = X.clone()
+    rc.rcqr_trsm(Y, R2, Q=Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(host64(Y), Qs)
