@@ -58,8 +58,8 @@ struct GemmCfg {
   static constexpr int OFF_SC = OFF_W + 3 * W_PIECE;        // column scales 2^(e_j - 14) of W (NP floats)
   static constexpr int OFF_MX = OFF_SC + NP * 4;            // row maxima of the half rows (TPR x 128 words)
   static constexpr int SMEM = OFF_MX + TPR * kGR * 4;
-  static constexpr uint32_t NCOLS = 2 * NP;                 // D_hh | D_s
-  static constexpr int CTAS = NP == 64 ? 3 : 1;
+  static constexpr uint32_t NCOLS = 4 * NP;                 // two tiles' D_hh | D_s
+  static constexpr int CTAS = NP == 64 ? 2 : 1;
   static_assert(CTAS * (SMEM + 2048) <= 228 * 1024, "CTAS CTAs per SM");
   static_assert(CTAS * NCOLS <= 512, "TMEM");
 };
@@ -173,7 +173,33 @@ __global__ void __launch_bounds__(GemmCfg<NP>::THREADS, GemmCfg<NP>::CTAS) gemm_
       y[c] = (lv && j < n) ? a.Y[rw + (int64_t)j * a.ldy] : 0.0f;
     }
   };
+  // Z = (D_hh + D_s) 2^(e_t - 14) 2^(e_j - 14) of a finished tile, this thread's row and half
+  auto readback = [&](uint32_t dbase, int64_t rw, bool lv, float rsc) {
+    int64_t ldz = a.ldz;
+    asm volatile("" : "+l"(ldz));
+#pragma unroll
+    for (int c16 = 0; c16 < 4; ++c16) {
+      uint32_t vh[16], vs[16];
+      const uint32_t col = (uint32_t)(64 * half + 16 * c16);
+      umma::tmem_ld16(lane_base + dbase + col, vh);
+      umma::tmem_ld16(lane_base + dbase + NP + col, vs);
+      umma::tmem_wait_ld();
+      if (lv) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = (int)col + u;
+          if (j < n) a.Z[rw + (int64_t)j * ldz] = (__uint_as_float(vh[u]) + __uint_as_float(vs[u])) * rsc * Isw[j];
+        }
+      }
+    }
+  };
+  // software pipeline: the MMAs of tile k (TMEM buffer k % 2) run while tile k - 1's
+  // results are read back from the other buffer
   load_tile(blockIdx.x);
+  uint32_t buf = 0;
+  bool have_prev = false, prev_live = false;
+  int64_t prev_row = 0;
+  float prev_isc = 0.0f;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * kGR + trow;
     const bool live = row < a.m;
@@ -187,7 +213,8 @@ __global__ void __launch_bounds__(GemmCfg<NP>::THREADS, GemmCfg<NP>::CTAS) gemm_
     }
     float sc, isc;                                     // the row's scale pair
     fixed_scales((int)(mx >> 23), sc, isc);
-    // the row pieces, K-major (piece p occupies K columns p NP .. p NP + NP - 1)
+    // the row pieces, K-major (piece p occupies K columns p NP .. p NP + NP - 1); the
+    // previous tile's MMAs, their last readers, completed in the previous iteration
 #pragma unroll
     for (int c8 = 0; c8 < 8; ++c8) {
       uint32_t hw[4], mw[4], lw[4];
@@ -201,11 +228,12 @@ __global__ void __launch_bounds__(GemmCfg<NP>::THREADS, GemmCfg<NP>::CTAS) gemm_
     load_tile(tile + gridDim.x);
     umma::fence_proxy_async();
     umma::fence_before_sync();
-    __syncthreads();
+    __syncthreads();   // the pieces written; the previous read-back of this TMEM buffer done
     if (tid == 0 && !*(volatile int *)&s_fail) {
       umma::fence_after_sync();
       // (row piece, W piece) of the leading product and of the seven next ones
       const int pa[8] = {0, 0, 1, 0, 1, 2, 1, 2}, pw[8] = {0, 1, 0, 2, 1, 0, 2, 1};
+      const uint32_t dbuf = tbase + buf * (2u * NP);
 #pragma unroll
       for (int t = 0; t < NP / 16; ++t) {
         const int N = NP - 16 * t;
@@ -214,36 +242,29 @@ __global__ void __launch_bounds__(GemmCfg<NP>::THREADS, GemmCfg<NP>::CTAS) gemm_
         for (int p = 0; p < 8; ++p) {
           const uint64_t ad = umma::smem_desc(ys_addr + ((pa[p] * NP + 16 * t) / 8) * 128, 128, C::YSBO);
           const uint64_t bd = umma::smem_desc(ws_addr + pw[p] * C::W_PIECE + w_region<NP>(t), 128, 256);
-          const uint32_t d = tbase + (p == 0 ? 0u : (uint32_t)NP) + 16u * t;
+          const uint32_t d = dbuf + (p == 0 ? 0u : (uint32_t)NP) + 16u * t;
           const bool first = t == 0 && (p == 0 || p == 1);
           umma::mma_bf16(d, ad, bd, id, first ? 0u : 1u);
         }
       }
       umma::mma_commit(&bar_mma);
     }
+    if (have_prev) {
+      umma::fence_after_sync();
+      readback((buf ^ 1u) * (2u * NP), prev_row, prev_live, prev_isc);
+    }
     wait_mma(&bar_mma, ph, &s_fail);
     ph ^= 1u;
-    umma::fence_after_sync();
-    // Z = (D_hh + D_s) 2^(e_t - 14) 2^(e_j - 14), this thread's row and half
-    int64_t ldz = a.ldz;
-    asm volatile("" : "+l"(ldz));
-#pragma unroll
-    for (int c16 = 0; c16 < 4; ++c16) {
-      uint32_t vh[16], vs[16];
-      const uint32_t col = (uint32_t)(64 * half + 16 * c16);
-      umma::tmem_ld16(lane_base + col, vh);
-      umma::tmem_ld16(lane_base + NP + col, vs);
-      umma::tmem_wait_ld();
-      if (live) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int j = (int)col + u;
-          if (j < n) a.Z[row + (int64_t)j * ldz] = (__uint_as_float(vh[u]) + __uint_as_float(vs[u])) * isc * Isw[j];
-        }
-      }
-    }
     umma::fence_before_sync();
-    __syncthreads();   // TMEM and the row-piece buffer are free for the next tile
+    have_prev = true;
+    prev_row = row;
+    prev_live = live;
+    prev_isc = isc;
+    buf ^= 1u;
+  }
+  if (have_prev) {
+    umma::fence_after_sync();
+    readback((buf ^ 1u) * (2u * NP), prev_row, prev_live, prev_isc);
   }
 
   // drain: every MMA issued by thread 0 has finished before TMEM is released
@@ -278,14 +299,48 @@ constexpr int kGramCols = 32;                 // columns per thread
 constexpr int kGramNP = 128;
 constexpr uint32_t kGramYSBO = (3 * kGramNP / 8) * 128;
 constexpr int kGramY = kGR * 3 * kGramNP * 2;  // 96 KB of pieces
-constexpr int kGramSmem = kGramY + 4 * kGramNP * 4 + 2 * kGramNP * 4;   // + warp maxima + scale pairs
+constexpr int kGramRaw = kGR * kGramNP * 4;      // one raw tile, column-major, 64 KB
+constexpr int kGramSmem = kGramRaw + kGramY + 4 * kGramNP * 4 + 2 * kGramNP * 4;   // raw, pieces, maxima, scales
+
+__device__ __forceinline__ void cp_async16z(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copies tile `tile` of Q (128 rows x n columns) into the raw buffer, column c at floats
+// c * 128 .. (rows past m read as zero): asynchronously in 16-byte pieces when Q's rows
+// are 16-byte aligned (vec), else by plain loads.
+__device__ __forceinline__ void gram_fetch_tile(const float *__restrict__ Q, int64_t m, int n, int64_t ldq,
+                                                int64_t tile, float *raw, bool vec) {
+  const int64_t r0 = tile * kGR;
+  for (int e = threadIdx.x; e < kGramNP * (kGR / 4); e += kGramThreads) {
+    const int c = e / (kGR / 4), q4 = e % (kGR / 4);
+    if (c >= n) continue;
+    const int64_t row = r0 + 4 * q4;
+    const int64_t left = m - row;
+    const int valid = left > 0 ? (int)(left < 4 ? left : 4) : 0;
+    float *dst = raw + c * kGR + 4 * q4;
+    if (vec) {
+      cp_async16z(dst, valid > 0 ? Q + row + (int64_t)c * ldq : Q, 4 * valid);
+    } else {
+      float v[4];
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) v[k4] = k4 < valid ? Q[row + k4 + (int64_t)c * ldq] : 0.0f;
+      *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+  cp_async_commit_all();
+}
 
 __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *__restrict__ Q, int64_t m, int n,
                                                                  int64_t ldq, double *partial, int *status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *Ys = smem;
-  unsigned *Wmax = reinterpret_cast<unsigned *>(smem + kGramY);         // 4 x NP: per warp row group
-  float *Sc = reinterpret_cast<float *>(smem + kGramY + 4 * kGramNP * 4), *Isc = Sc + kGramNP;
+  float *raw = reinterpret_cast<float *>(smem);
+  unsigned char *Ys = smem + kGramRaw;
+  unsigned *Wmax = reinterpret_cast<unsigned *>(smem + kGramRaw + kGramY);      // 4 x NP: per warp row group
+  float *Sc = reinterpret_cast<float *>(smem + kGramRaw + kGramY + 4 * kGramNP * 4), *Isc = Sc + kGramNP;
   __shared__ uint64_t bar_mma, bar_drain;
   __shared__ uint32_t tslot;
   __shared__ int s_fail;
@@ -293,6 +348,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int trow = tid % kGR, grp = tid / kGR;          // row of the tile, column group
   const int c0 = kGramCols * grp;
+  const bool vec = ((uintptr_t)Q % 16 == 0) && (ldq % 4 == 0);
   if (tid == 0) {
     umma::mbar_init(&bar_mma, 1);
     umma::mbar_init(&bar_drain, 1);
@@ -311,16 +367,18 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *_
   for (int c = 0; c < kGramCols; ++c) acc[c] = cmp[c] = 0.0f;
   uint32_t ph = 0;
 
+  // per tile: split the raw tile (copied during the previous tile's MMAs and fold),
+  // start the copy of the next tile, run the MMAs, fold
   const int64_t tiles = (m + kGR - 1) / kGR;
+  if ((int64_t)blockIdx.x < tiles) gram_fetch_tile(Q, m, n, ldq, blockIdx.x, raw, vec);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * kGR + trow;
     const bool live = row < m;
+    cp_async_wait_all();
+    __syncthreads();                                    // the raw tile is complete
     float y[kGramCols];
 #pragma unroll
-    for (int c = 0; c < kGramCols; ++c) {
-      const int j = c0 + c;
-      y[c] = (live && j < n) ? Q[row + (int64_t)j * ldq] : 0.0f;
-    }
+    for (int c = 0; c < kGramCols; ++c) y[c] = (live && c0 + c < n) ? raw[(c0 + c) * kGR + trow] : 0.0f;
     // per column, the tile's largest |q|: warp maxima, then the four row groups
 #pragma unroll
     for (int c = 0; c < kGramCols; ++c) {
@@ -348,25 +406,28 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *_
     }
     umma::fence_proxy_async();
     umma::fence_before_sync();
-    __syncthreads();
+    __syncthreads();                                    // pieces written; the raw buffer is free
     if (tid == 0 && !*(volatile int *)&s_fail) {
       umma::fence_after_sync();
-      // MN-major views of the pieces: 8-column groups 128 B apart (SBO), 8-row groups
-      // kGramYSBO apart (LBO); (A piece, B piece, accumulator)
-      const uint32_t id = umma::idesc_f16_f32(kGR, kGramNP) | (1u << 15) | (1u << 16);
-      const int pa[4] = {0, 0, 0, 1}, pb[4] = {0, 1, 2, 1};
+      // MN-major views: 8-column groups 128 B apart (SBO), 8-row groups kGramYSBO apart
+      // (LBO); per K-step H^T [H | M] (N = 256: the H and M pieces are adjacent),
+      // H^T L, M^T M
+      const uint32_t id256 = umma::idesc_f16_f32(kGR, 2 * kGramNP) | (1u << 15) | (1u << 16);
+      const uint32_t id128 = umma::idesc_f16_f32(kGR, kGramNP) | (1u << 15) | (1u << 16);
 #pragma unroll
       for (int t = 0; t < kGR / 16; ++t) {
         const uint32_t kofs = (uint32_t)(2 * t) * kGramYSBO;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const uint64_t ad = umma::smem_desc(ys_addr + kofs + ((pa[p] * kGramNP) / 8) * 128, kGramYSBO, 128);
-          const uint64_t bd = umma::smem_desc(ys_addr + kofs + ((pb[p] * kGramNP) / 8) * 128, kGramYSBO, 128);
-          umma::mma_bf16(tbase + (uint32_t)(p * kGramNP), ad, bd, id, t > 0 ? 1u : 0u);
-        }
+        const uint64_t dh = umma::smem_desc(ys_addr + kofs, kGramYSBO, 128);
+        const uint64_t dm = umma::smem_desc(ys_addr + kofs + (kGramNP / 8) * 128, kGramYSBO, 128);
+        const uint64_t dl = umma::smem_desc(ys_addr + kofs + (2 * kGramNP / 8) * 128, kGramYSBO, 128);
+        const uint32_t acc_flag = t > 0 ? 1u : 0u;
+        umma::mma_bf16(tbase, dh, dh, id256, acc_flag);                    // hh | hm
+        umma::mma_bf16(tbase + 2 * kGramNP, dh, dl, id128, acc_flag);      // hl
+        umma::mma_bf16(tbase + 3 * kGramNP, dm, dm, id128, acc_flag);      // mm
       }
       umma::mma_commit(&bar_mma);
     }
+    if (tile + gridDim.x < tiles) gram_fetch_tile(Q, m, n, ldq, tile + gridDim.x, raw, vec);
     wait_mma(&bar_mma, ph, &s_fail);
     ph ^= 1u;
     umma::fence_after_sync();
@@ -395,6 +456,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_tc_kernel(const float *_
     umma::fence_before_sync();
     __syncthreads();   // TMEM, the pieces and the scales are free for the next tile
   }
+  cp_async_wait_all();
   // the CTA's partial S (row i = trow, this thread's columns), in FP64
   const bool failed = *(volatile int *)&s_fail != 0;
   if (trow < n) {
