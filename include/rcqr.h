@@ -315,7 +315,8 @@ rcqr_status rcqr_reduced(const void *X, int64_t m, int64_t n, int64_t ldx, int p
  * (same type as Q), Rbar (double, n x n, upper triangle used) the incoming
  * gradients; Xbar (type of Q) receives the gradient.  prec: RCQR_F64 (double
  * data, FP64) or RCQR_F32 (float data, FP32 rows with a compensated Qbar^T Q).
- * Workspace: rcqr_qr_adjoint_workspace_size(m, n) bytes. */
+ * Workspace: rcqr_qr_adjoint_workspace_size(m, n) bytes (it holds an m x n buffer for
+ * Y = Qbar + Q copyltu(M) besides the n x n matrices). */
 size_t rcqr_qr_adjoint_workspace_size(int64_t m, int64_t n);
 rcqr_status rcqr_qr_adjoint(const void *Q, int64_t m, int64_t n, int64_t ldq, int prec, const double *R,
                             int64_t ldr, const void *Qbar, int64_t ldqb, const double *Rbar, int64_t ldrb,
