@@ -52,8 +52,18 @@ constexpr int OFF_RD = OFF_R + 3 * kWRPiece;            // diagonal blocks, kWB 
 constexpr int OFF_DS = OFF_RD + kWB * 256 * 4;          // fl32(1 / R_jj)
 constexpr int OFF_SRC = OFF_DS + kWN * 4;               // source column of X per column
 constexpr int kWSmem = OFF_SRC + kWN * 4;
+// BF16 X: the tile is staged in shared memory (column c of the tile at bytes 256 c),
+// copied in 16-byte pieces while the previous tile is solved: the threads' own 2-byte
+// loads of a row along the columns used half of every memory transaction
+constexpr int OFF_XS = kWSmem;
+constexpr int kWSmemBf16 = OFF_XS + kWR * kWN * 2;
 constexpr int kWCtas = 2;
-static_assert(kWCtas * (kWSmem + 2048) <= 228 * 1024, "CTAs per SM");
+static_assert(kWCtas * (kWSmemBf16 + 2048) <= 228 * 1024, "CTAs per SM");
+
+__device__ __forceinline__ void cp_async16w(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(umma::smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
 
 struct TcwArgs {
   const void *X;
@@ -67,6 +77,7 @@ struct TcwArgs {
   float *Q;
   int64_t ldq;
   int *status;          // nullable: RCQR_ETIMEOUT on a wait that gave up
+  int vec;              // BF16 X: rows 16-byte aligned (the staged copy uses 16-byte pieces)
 };
 
 __device__ __forceinline__ float to_f32w(float x) { return x; }
@@ -147,14 +158,41 @@ __global__ void __launch_bounds__(kWR, kWCtas) trsm_tcw_kernel(TcwArgs a) {
   uint32_t ph = 0;
 
   const int64_t tiles = (a.m + kWR - 1) / kWR;
+  constexpr bool kStage = sizeof(TX) == 2;
+  __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(smem + OFF_XS);
+  // BF16: copies tile tl (its columns in Src order) into Xs, rows past m read as zero
+  auto stage = [&](int64_t tl) {
+    const int64_t r0 = tl * kWR;
+    for (int e = tid; e < kWN * (kWR / 8); e += kWR) {
+      const int c = e / (kWR / 8), q8 = e % (kWR / 8);
+      const int src = Src[c];
+      if (src < 0) continue;
+      const int64_t rw = r0 + 8 * q8;
+      const int64_t left = a.m - rw;
+      const int valid = left > 0 ? (int)(left < 8 ? left : 8) : 0;
+      const TX *g = X + rw + (int64_t)src * a.ldx;
+      cp_async16w(Xs + c * kWR + 8 * q8, valid > 0 ? (const void *)g : (const void *)X, 2 * valid);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (kStage && a.vec && (int64_t)blockIdx.x < tiles) stage(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * kWR + tid;
     const bool live = row < a.m;
     float q[kWN];
+    if (kStage && a.vec) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kWN; ++j) {
-      const int src = Src[j];
-      q[j] = (live && src >= 0) ? to_f32w(X[row + (int64_t)src * a.ldx]) : 0.0f;
+      for (int j = 0; j < kWN; ++j) q[j] = (live && Src[j] >= 0) ? __bfloat162float(Xs[j * kWR + tid]) : 0.0f;
+      __syncthreads();                                   // Xs read by every thread: copy the next tile
+      if (tile + gridDim.x < tiles) stage(tile + gridDim.x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kWN; ++j) {
+        const int src = Src[j];
+        q[j] = (live && src >= 0) ? to_f32w(X[row + (int64_t)src * a.ldx]) : 0.0f;
+      }
     }
 #pragma unroll
     for (int J = 0; J < kWB; ++J) {
@@ -257,13 +295,14 @@ bool trsm_tcw_supported(int64_t n) { return n > 64 && n <= 128; }
 cudaError_t launch_trsm_tcw(const void *X, int64_t m, int64_t n, int64_t ldx, int prec, const float *Rf,
                             const float *dinv, const int32_t *perm, const int64_t *rank, float *Q, int64_t ldq,
                             int *status, cudaStream_t st) {
-  TcwArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, status};
+  const int vec = ((uintptr_t)X % 16 == 0) && (ldx % 8 == 0);
+  TcwArgs a{X, m, (int)n, ldx, Rf, dinv, perm, rank, Q, ldq, status, vec};
   const int64_t tiles = (m + kWR - 1) / kWR;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kWCtas * num_sms()));
   cudaError_t e;
   if (prec == RCQR_BF16) {
-    if ((e = set_smem(trsm_tcw_kernel<__nv_bfloat16>, kWSmem)) != cudaSuccess) return e;
-    trsm_tcw_kernel<__nv_bfloat16><<<grid, kWR, kWSmem, st>>>(a);
+    if ((e = set_smem(trsm_tcw_kernel<__nv_bfloat16>, kWSmemBf16)) != cudaSuccess) return e;
+    trsm_tcw_kernel<__nv_bfloat16><<<grid, kWR, kWSmemBf16, st>>>(a);
   } else {
     if ((e = set_smem(trsm_tcw_kernel<float>, kWSmem)) != cudaSuccess) return e;
     trsm_tcw_kernel<float><<<grid, kWR, kWSmem, st>>>(a);
