@@ -275,8 +275,11 @@ def test_factor_direct_parity(rc, inputs, prec, variant, m, n, k, cond):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("variant", [2, 3])
-def test_factor_rank_revealing_parity(rc, inputs, prec, variant):
-    m, n, r, k = 20000, 32, 16, 128
+@pytest.mark.parametrize("n", [32, 96])
+def test_factor_rank_revealing_parity(rc, inputs, prec, variant, n):
+    # n = 96 on the mixed path: the wide tensor-core substitution with the permutation and
+    # the rank, and for RR2 the tensor-core Gram and the pass-2 product (zero beyond the rank)
+    m, r, k = 20000, n // 2, 4 * n
     X = inputs.rank_deficient(m, n, r, 77, noise=1e-12, dtype=prec, device=DEV)
     tau = 1e-10 if prec == "f64" else 1e-5
     seed = 99
@@ -289,14 +292,23 @@ def test_factor_rank_revealing_parity(rc, inputs, prec, variant):
         Qo, Ro, permo, ro = orc.rrrcholqr2(Xh, k, seed, tau)
     assert int(status[0]) == 0
     assert int(rank[0]) == ro == r
-    assert perm.cpu().numpy().tolist() == permo.tolist()
+    # the kept columns are decided by clear norm gaps; beyond the rank the remaining column
+    # norms are noise of the size of the rounding (1e-12 relative), where the order of
+    # near-ties may differ: compared as a set there
+    pg = perm.cpu().numpy()
+    assert pg[:r].tolist() == permo[:r].tolist()
+    assert sorted(pg.tolist()) == list(range(n))
     Qg, Rg = host64(Q), host64(R)
     assert np.all(Qg[:, r:] == 0) and np.all(Rg[r:] == 0)
     uq = U if prec == "f64" else 2.0 ** -24
     D = np.linalg.norm(Xh, axis=0)
-    E = (Xh[:, permo] - Qg[:, :r] @ Rg[:r]) / D[permo][None, :]
+    E = (Xh[:, pg] - Qg[:, :r] @ Rg[:r]) / D[pg][None, :]
     assert np.linalg.norm(E) <= 2 * tau + 100 * uq
-    assert colrel(Qg[:, :r] @ Rg[:r], Qo @ Ro) <= max(1e-10, 100 * uq)
+    # the two factorizations' products, each with its columns put back in X's order
+    Pg, Po = np.empty_like(Xh), np.empty_like(Xh)
+    Pg[:, pg] = Qg[:, :r] @ Rg[:r]
+    Po[:, permo] = Qo @ Ro
+    assert colrel(Pg, Po) <= max(1e-10, 100 * uq)
     if variant == 3:
         assert orc.orthogonality(Qg[:, :r]) <= max(1e-12, 100 * r * uq)
 
