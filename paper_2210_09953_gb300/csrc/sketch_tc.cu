@@ -663,47 +663,71 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     const bool rademacher = a.dist == RCQR_THETA_RADEMACHER;
     if (rademacher) rad.init(tid, kgi);
     else calls.init(tid, kgi);
+    // ring slot, its phase parity, block and stage within the block, first X row of
+    // the stage: all advanced incrementally (blocks are contiguous, so the row is
+    // bb BR + it kBK)
+    int slot = 0, b = 0, st = 0;
+    uint32_t ph = 0;
+    int64_t r0 = bb * kBlockRows;
     for (int it = 0; it < total; ++it) {
-      const int slot = it % D;
-      const int b = it / kSPB, st = it % kSPB;
       // the ring holds the next block's first D stages: fold the previous block (the
       // next slot is released only by MMAs issued after that fold)
       if (st == D && b > 0) K::fold(sh, b - 1, NB, tbase, Acc, a, kgi, col0, g, bb + b - 1);
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
-      const int64_t r0 = (bb + b) * kBlockRows + st * kBK;
+      if (it >= D) wait_or_fail(&sh.empty[slot], ph ^ 1u, &sh.s_fail, 256, a.polls);
       if (rademacher) rad.tile(stage_base + slot * K::STAGE_BYTES, r0, a);
       else calls.tile(stage_base + slot * K::STAGE_BYTES, tabp, r0, a);
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
+      r0 += kBK;
+      if (++slot == D) { slot = 0; ph ^= 1u; }
+      if (++st == kSPB) { st = 0; ++b; }
     }
     if (NB > 0) K::fold(sh, NB - 1, NB, tbase, Acc, a, kgi, col0, g, bb + NB - 1);
   } else if (warp < kProdWarps) {
     // ---- X producers: task o = xt + NXT u is column jl = 8 (o / 32) + o % 8, octet oc = (o / 8) % 4
     // (8 consecutive lanes: 8 consecutive columns of one octet, so the slice stores do not conflict)
     const int xt = tid - 32 * NTW;
-    // copies the octet of task o for stage s into ring slot `slot` (asynchronously where possible)
-    auto issue = [&](int s, int slot, int o) {
+    // per task: its column (j < n, else zeros), its 8-row octet, the row of that octet
+    // in the CTA's first stage; a stage s adds s kBK rows (blocks are contiguous)
+    static_assert((kXSlots & (kXSlots - 1)) == 0, "X ring slots: a power of two");
+    const T *colp[TPT];
+    int64_t lrb[TPT];
+    bool fast[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int o = xt + NXT * u;
       const int jl = 8 * (o >> 5) + (o & 7), oc = (o >> 3) & 3;
       const int j = col0 + jl;
-      const int64_t lr0 = (bb + s / kSPB) * kBlockRows + (s % kSPB) * kBK + 8 * oc - a.row_offset;
-      unsigned char *dst = xring + slot * SLOT_BYTES + o * 16;
-      if (j < a.n && a.vec && lr0 >= 0 && lr0 + 8 <= a.m) {
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(X + lr0 + (int64_t)j * a.ldx);
+      colp[u] = X + (int64_t)(j < a.n ? j : 0) * a.ldx;
+      lrb[u] = bb * kBlockRows - a.row_offset + 8 * oc;
+      fast[u] = j < a.n && a.vec;
+    }
+    // copies the octets of stage s into ring slot s mod kXSlots (asynchronously where possible)
+    auto issue = [&](int s) {
+      unsigned char *slot_base = xring + (s & (kXSlots - 1)) * SLOT_BYTES;
 #pragma unroll
-        for (int h = 0; h < H; ++h) cp_async16(dst + h * (NTASK * 16), src + 16 * h);
-      } else {
-        __align__(16) T v[8];
-        load8<T>(X, lr0, j, a, v);
+      for (int u = 0; u < TPT; ++u) {
+        const int o = xt + NXT * u;
+        const int64_t lr0 = lrb[u] + (int64_t)s * kBK;
+        unsigned char *dst = slot_base + o * 16;
+        if (fast[u] && lr0 >= 0 && lr0 + 8 <= a.m) {
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(colp[u] + lr0);
 #pragma unroll
-        for (int h = 0; h < H; ++h) *reinterpret_cast<uint4 *>(dst + h * (NTASK * 16)) = reinterpret_cast<const uint4 *>(v)[h];
+          for (int h = 0; h < H; ++h) cp_async16(dst + h * (NTASK * 16), src + 16 * h);
+        } else {
+          const int jl = 8 * (o >> 5) + (o & 7);
+          __align__(16) T v[8];
+          load8<T>(X, lr0, col0 + jl, a, v);
+#pragma unroll
+          for (int h = 0; h < H; ++h)
+            *reinterpret_cast<uint4 *>(dst + h * (NTASK * 16)) = reinterpret_cast<const uint4 *>(v)[h];
+        }
       }
     };
 #pragma unroll 1
     for (int s = 0; s < kXAhead; ++s) {
-      if (s < total)
-#pragma unroll
-        for (int u = 0; u < TPT; ++u) issue(s, s % kXSlots, xt + NXT * u);
+      if (s < total) issue(s);
       cp_async_commit();
     }
     int e_cur[TPT], e_nxt[TPT];
@@ -714,13 +738,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       e_cur[u] = col0 + jl < a.n ? a.eblk[(bb - a.blk0) * a.n + col0 + jl] : EMPTY_EXP;
       e_nxt[u] = e_cur[u];
     }
+    int slot = 0, b = 0, st = 0;
+    uint32_t ph = 0;
     for (int it = 0; it < total; ++it) {
-      const int slot = it % D;
-      const int b = it / kSPB, st = it % kSPB;
       if (st == D && b > 0) K::fold(sh, b - 1, NB, tbase, Acc, a, kgi, col0, g, bb + b - 1);
-      if (it + kXAhead < total)
-#pragma unroll
-        for (int u = 0; u < TPT; ++u) issue(it + kXAhead, (it + kXAhead) % kXSlots, xt + NXT * u);
+      if (it + kXAhead < total) issue(it + kXAhead);
       cp_async_commit();
       if (st == kSPB / 2 && b + 1 < NB) {
         // exponents of the next block, read early
@@ -736,9 +758,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
         for (int u = 0; u < TPT; ++u) e_cur[u] = e_nxt[u];
       }
       cp_async_wait<kXAhead>();
-      if (it >= D) wait_or_fail(&sh.empty[slot], (uint32_t)((it / D - 1) & 1), &sh.s_fail, 256, a.polls);
+      if (it >= D) wait_or_fail(&sh.empty[slot], ph ^ 1u, &sh.s_fail, 256, a.polls);
       unsigned char *sB = stage_base + slot * K::STAGE_BYTES + K::A_BYTES;
-      const unsigned char *src = xring + (it % kXSlots) * SLOT_BYTES;
+      const unsigned char *src = xring + (it & (kXSlots - 1)) * SLOT_BYTES;
 #pragma unroll
       for (int u = 0; u < TPT; ++u) {
         const int o = xt + NXT * u;
@@ -752,6 +774,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       umma::fence_proxy_async();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&sh.full[slot]);
+      if (++slot == D) { slot = 0; ph ^= 1u; }
+      if (++st == kSPB) { st = 0; ++b; }
     }
     cp_async_wait<0>();
     if (NB > 0) K::fold(sh, NB - 1, NB, tbase, Acc, a, kgi, col0, g, bb + NB - 1);
@@ -765,33 +789,36 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     // Theta tile is then read once for all of them); the slices below NE add
     // into accumulator NE one MMA each.
     constexpr int G = 256 / NC;
+    // operand descriptors of ring slot 0; a slot, chunk, K step or slice adds its byte
+    // offset / 16 to the start-address field (shared addresses stay below 2^18 bytes,
+    // so the 14-bit field does not carry)
+    const uint64_t desc0 = umma::smem_desc(umma::smem_u32(stage_base), 128, kBK * 16);
+    int slot = 0, b = 0, st = 0;
+    uint32_t ph = 0;
     for (int it = 0; it < total; ++it) {
-      const int slot = it % D;
-      const int b = it / kSPB, st = it % kSPB;
       // once any wait of the CTA has given up, no further MMA is issued (the partial sums
       // become NaN below), so nothing new is in flight when TMEM is released
-      if (lane == 0) wait_or_fail(&sh.full[slot], (uint32_t)((it / D) & 1), &sh.s_fail, 64, a.polls);
+      if (lane == 0) wait_or_fail(&sh.full[slot], ph, &sh.s_fail, 64, a.polls);
       if (lane == 0 && *(volatile int *)&sh.s_fail == 0) {
         umma::fence_after_sync();
-        const uint32_t a0 = umma::smem_u32(stage_base + slot * K::STAGE_BYTES);
-        const uint32_t b0 = a0 + K::A_BYTES;
+        const uint64_t dslot = desc0 + (uint64_t)((slot * K::STAGE_BYTES) >> 4);
 #pragma unroll
         for (int c = 0; c < KCH; ++c)
 #pragma unroll
           for (int q = 0; q < kBK / 16; ++q) {
-            const uint64_t ad = umma::smem_desc(a0 + c * (128 * kBK * 2) + q * 256, 128, kBK * 16);
+            const uint64_t ad = dslot + (uint64_t)((c * (128 * kBK * 2) + q * 256) >> 4);
             const bool first = (st == 0) && (q == 0);
 #pragma unroll
             for (int g0 = 0; g0 <= K::NE; g0 += G) {
               const int cnt = (K::NE + 1 - g0) < G ? (K::NE + 1 - g0) : G;
               const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + g0) * NC);
-              const uint64_t bd = umma::smem_desc(b0 + g0 * (NC * kBK * 2) + q * 256, 128, kBK * 16);
+              const uint64_t bd = dslot + (uint64_t)((K::A_BYTES + g0 * (NC * kBK * 2) + q * 256) >> 4);
               umma::mma_bf16(dcol, ad, bd, umma::idesc_bf16_f32(128, cnt * NC), first ? 0u : 1u);
             }
 #pragma unroll
             for (int bs = K::NE + 1; bs < S; ++bs) {
               const uint32_t dcol = tbase + (uint32_t)((c * K::NACC + K::NE) * NC);
-              const uint64_t bd = umma::smem_desc(b0 + bs * (NC * kBK * 2) + q * 256, 128, kBK * 16);
+              const uint64_t bd = dslot + (uint64_t)((K::A_BYTES + bs * (NC * kBK * 2) + q * 256) >> 4);
               umma::mma_bf16(dcol, ad, bd, umma::idesc_bf16_f32(128, NC), 1u);
             }
           }
@@ -800,6 +827,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
       }
       __syncwarp();
       if (st == kSPB - 1) K::fold(sh, b, NB, tbase, Acc, a, kgi, col0, g, bb + b);
+      if (++slot == D) { slot = 0; ph ^= 1u; }
+      if (++st == kSPB) { st = 0; ++b; }
     }
     // drain: the barrier completes once every MMA this thread issued has finished
     // writing TMEM (at once if none was issued); bounded by the default limit, so a
