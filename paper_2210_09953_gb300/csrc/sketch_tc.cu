@@ -18,8 +18,9 @@
 // of 5 slices) / 2^-46 (FP64 X: 4 exact of 8) below the block's largest |x|;
 // BF16 X needs 3 slices.  After every block the accumulators are read from
 // TMEM, combined into one int64 per entry and added into a per-column
-// block-floating-point int64 accumulator (the "simple addition" of Sec. 3.1
-// done exactly, up to one truncation of ~2^-52 relative per block).
+// block-floating-point int64 accumulator whose exponent is fixed per CTA (the
+// largest block exponent of its rows; the "simple addition" of Sec. 3.1 done
+// exactly, up to one truncation of ~2^-52 of that column's largest entry per block).
 //
 // Per CTA: a contiguous run of blocks (split-K over m), KCH chunks of 128
 // rows of Theta and NC columns of X.  The CTA's 16 warps are specialised
@@ -434,8 +435,8 @@ struct Tc {
     uint64_t drain;      // completion of the MMA thread's last MMAs, before TMEM is released
     uint32_t tslot;
     int s_fail;
-    int E_col[2][NC];    // running exponents of the int64 accumulators (by block parity)
-    int e_blk[NC];       // the folded block's column exponents
+    int E_fix[NC];       // the int64 accumulators' column exponents: the largest block exponent of the CTA's rows
+    int sft[NC];         // the folded block's right shift onto them (0 for an all-zero block column)
   };
 
   // Folds block b's TMEM accumulators into the int64 accumulators.  Run by all
@@ -462,12 +463,15 @@ struct Tc {
       for (int h = 0; h < 4; ++h) nxt[h] = acc_ptr(part)[h];
     }
     const int *eb = a.eblk + (blk - a.blk0) * a.n;
-    for (int jl = tid; jl < NC; jl += kThreadsTC) sh.e_blk[jl] = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
+    for (int jl = tid; jl < NC; jl += kThreadsTC) {
+      const int e = col0 + jl < a.n ? __ldg(eb + col0 + jl) : EMPTY_EXP;
+      const int d = sh.E_fix[jl] - e;
+      sh.sft[jl] = e == EMPTY_EXP ? 0 : (d < 63 ? d : 63);
+    }
     wait_or_fail(&sh.accf, (uint32_t)(b & 1), &sh.s_fail, 256, a.polls);
     umma::fence_after_sync();
     umma::named_sync(kThreadsTC);
     const bool last = b == NB - 1;
-    const int p = b & 1;
 #pragma unroll 1
     for (int ch = part; ch < NCH; ch += 4) {
       const int c = ch / CPC, jc0 = (ch % CPC) * 8;
@@ -488,39 +492,21 @@ struct Tc {
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
         const int jl = jc0 + jj;
-        const int e = sh.e_blk[jl];
-        const int Ec = sh.E_col[p][jl];
         const long long old = b > 0 ? ((jj & 1) ? old2[jj >> 1].y : old2[jj >> 1].x) : 0LL;
-        long long acc_v;
-        int En;
-        if (e == EMPTY_EXP) {
-          En = Ec;
-          acc_v = Ec == EMPTY_EXP ? 0LL : old;
-        } else {
-          long long V = 0;
+        // the block's value in units of 2^(e - TOP - 7 NE - LS) (an all-zero block column
+        // gives 0), then shifted onto the CTA's column exponent (floor, as the int64 sum)
+        long long V = 0;
 #pragma unroll
-          for (int bs = 0; bs < NE; ++bs)
-            V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
-          V += rint_to_ll(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));   // |.| < 2^35
-          const int f = e - TOP - 7 * NE - LS;
-          if (Ec == EMPTY_EXP) {
-            acc_v = V;
-            En = f;
-          } else if (f >= Ec) {
-            const int sft = f - Ec;
-            acc_v = (sft >= 63 ? (old < 0 ? -1LL : 0LL) : (old >> sft)) + V;
-            En = f;
-          } else {
-            const int sft = Ec - f;
-            acc_v = old + (sft >= 63 ? (V < 0 ? -1LL : 0LL) : (V >> sft));
-            En = Ec;
-          }
-        }
+        for (int bs = 0; bs < NE; ++bs)
+          V += (long long)__float2int_rn(__uint_as_float(rv[bs][jj]) * pow2f(7 * bs)) << (7 * (NE - bs) + LS);
+        V += rint_to_ll(__uint_as_float(rv[NE][jj]) * pow2f(7 * NE + LS));   // |.| < 2^35
+        const long long acc_v = old + (V >> sh.sft[jl]);
         out[jj] = acc_v;
         if (last) {
           const int j = col0 + jl;
+          const int E = sh.E_fix[jl];
           if (i < a.k && j < a.n)
-            a.partial[((int64_t)g * a.n + j) * a.k + i] = En == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, En);
+            a.partial[((int64_t)g * a.n + j) * a.k + i] = E == EMPTY_EXP ? 0.0 : ldexp((double)acc_v, E - TOP - 7 * NE - LS);
         }
       }
       if (!last) {
@@ -528,17 +514,6 @@ struct Tc {
 #pragma unroll
         for (int h = 0; h < 4; ++h) ap[h] = make_longlong2(out[2 * h], out[2 * h + 1]);
       }
-    }
-    // running exponents after this block
-    for (int jl = tid; jl < NC; jl += kThreadsTC) {
-      const int e = sh.e_blk[jl];
-      const int Ec = sh.E_col[p][jl];
-      int En = Ec;
-      if (e != EMPTY_EXP) {
-        const int f = e - TOP - 7 * NE - LS;
-        En = (Ec == EMPTY_EXP || f > Ec) ? f : Ec;
-      }
-      sh.E_col[p ^ 1][jl] = En;
     }
     umma::fence_before_sync();
     umma::named_sync(kThreadsTC);
@@ -639,7 +614,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     const int lev = (int)a.theta.level[e >> 5];
     table[e] = __float_as_uint((float)lev) >> 16;
   }
-  for (int j = tid; j < NC; j += kThreadsTC) sh.E_col[0][j] = EMPTY_EXP;
+  for (int j = tid; j < NC; j += kThreadsTC) sh.E_fix[j] = EMPTY_EXP;
   if (tid == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       umma::mbar_init(&sh.full[s], kProdWarps);
@@ -654,6 +629,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tbase = sh.tslot;
+  {
+    // column exponents of the int64 accumulators: the largest block exponent over the
+    // CTA's blocks (fixed, so each block's value is shifted onto them once)
+    static_assert(kThreadsTC % NC == 0, "whole columns per thread group");
+    const int jl = tid % NC;
+    if (col0 + jl < a.n) {
+      int mx = EMPTY_EXP;
+      for (int b = tid / NC; b < NB; b += kThreadsTC / NC) mx = max(mx, __ldg(a.eblk + (bb - a.blk0 + b) * a.n + col0 + jl));
+      atomicMax(&sh.E_fix[jl], mx);
+    }
+  }
+  __syncthreads();
 
   if (warp < NTW) {
     // ---- Theta producers
