@@ -39,9 +39,9 @@ ORACLE_ROWS = 1 << 22          # the CPU oracle's sample: the whole matrix (abou
 # (dram__bytes_read.sum + dram__bytes_write.sum of every kernel of the call, captured on a
 # 1M-row launch and scaled by 4: per-row traffic is the same).  None where the kernels
 # changed after the last capture.
-TRAFFIC = {"sketch": 4 * (268455680 + 190208 + 288155648 + 26288128 + 19934464),
-           "trsm_gram": 4 * (26624 + 268855552 + 225936384 + 6237696),
-           "trsm": 4 * (26880 + 268603648 + 204486656)}
+TRAFFIC = {"sketch": 4 * (268463168 + 1105536 + 286893696 + 24914688 + 19934720),
+           "trsm_gram": 4 * (27721 + 268700608 + 225607168 + 6237888),
+           "trsm": 4 * (27721 + 268585643 + 204263595)}
 
 
 def parse():
