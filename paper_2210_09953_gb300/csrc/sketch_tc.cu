@@ -441,8 +441,8 @@ struct Tc {
 
   // Folds block b's TMEM accumulators into the int64 accumulators.  Run by all
   // 16 warps of the CTA (the producers join once they have filled the ring with
-  // the next block's first stages, so the fold is off no one's critical path but
-  // the MMA thread's): warp w reads TMEM lanes 32 (w % 4) .. (its lane quadrant)
+  // the next block's first stages: no further slot frees up before the fold has
+  // read TMEM and the next MMAs run): warp w reads TMEM lanes 32 (w % 4) .. (its lane quadrant)
   // and takes every fourth 8-column chunk, starting at chunk w / 4; each thread
   // owns one Theta row of its chunks.  Starts and ends with a barrier of the
   // whole CTA, after which TMEM may be overwritten.
