@@ -29,6 +29,23 @@ bit per entry:
   bit b being bit (b mod 32) of word floor(b/32);
 * Theta(i, r) = (1 - 2 bit) / sqrt(k): +-1/sqrt(k), so E[Theta^T Theta] = I and
   every column of Theta has unit norm exactly.
+
+The subsampled randomized Hadamard transform (SRHT, Sec. 2: random signs, a
+Hadamard matrix over X's rows padded with zeros to a power of two, uniform row
+sampling, the factor sqrt(1/k)) is written out as its definition
+Theta = sqrt(1/k) S H D (a reading; the paper fixes no bit stream and no order):
+* D = diag(d_r): d_r = 1 - 2 bit, bit (r mod 128) of the Philox4x32-10 output for
+      counter = (floor(r/128) mod 2^32, floor(r/128) div 2^32, 2^32 - 1, stream)
+  (the Rademacher bit stream at the row index 2^32 - 1, which no Theta row takes);
+* H is the Sylvester-Hadamard matrix of order 2^64 (X padded with zero rows):
+  H(h, r) = (-1)^popcount(h AND r);
+* S samples k rows of H uniformly, with replacement: Theta row i takes Hadamard row
+      h_i = w0 + 2^32 w1,  (w0, w1) the first two words of the Philox output for
+      counter = (i, 0, 2^32 - 2, stream);
+* Theta(i, r) = d_r (-1)^popcount(h_i AND r) / sqrt(k).  Every column has unit norm
+  exactly and E[Theta^T Theta] = I.  Over any 2^p aligned rows of X, two rows of
+  Theta whose h differ modulo 2^p are orthogonal, and two whose h agree are equal
+  up to sign.
 """
 import numpy as np
 from scipy.special import ndtri
@@ -116,16 +133,54 @@ def rademacher_signs(seed, k, row_offset, m, stream=0, rows=None):
     return 1.0 - 2.0 * bits[:, start:start + m]
 
 
+SRHT = "srht"
+SRHT_SIGN_ROW = 0xFFFFFFFF       # the counter word of the SRHT's sign stream D
+SRHT_ROW_TAG = 0xFFFFFFFE        # the counter word of its row sampling S
+
+
+def srht_rows(seed, k, stream=0, rows=None):
+    """The sampled Hadamard row h_i (uint64) of every Theta row i (S of the SRHT)."""
+    sel = np.arange(k) if rows is None else np.asarray(rows)
+    i = sel.astype(np.uint64)
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    w = philox4x32_10(i, np.uint64(0), np.uint64(SRHT_ROW_TAG), np.uint64(stream),
+                      seed & 0xFFFFFFFF, seed >> 32)
+    return w[0].astype(np.uint64) | (w[1].astype(np.uint64) << np.uint64(32))
+
+
+def parity64(v):
+    """popcount(v) mod 2 of uint64 values, by folding."""
+    v = np.asarray(v, dtype=np.uint64).copy()
+    for s in (32, 16, 8, 4, 2, 1):
+        v ^= v >> np.uint64(s)
+    return (v & np.uint64(1)).astype(np.int64)
+
+
+def srht_signs(seed, k, row_offset, m, stream=0, rows=None):
+    """The k x m array of +-1 (float64) of the SRHT, d_r (-1)^popcount(h_i AND r), for
+    rows r = row_offset .. row_offset+m-1 of X."""
+    sel = np.arange(k) if rows is None else np.asarray(rows)
+    if m == 0:
+        return np.zeros((len(sel), 0))
+    d = rademacher_signs(seed, 1, row_offset, m, stream, rows=[SRHT_SIGN_ROW])[0]
+    h = srht_rows(seed, k, stream, sel)
+    r = np.arange(row_offset, row_offset + m, dtype=np.uint64)
+    par = parity64(h[:, None] & r[None, :])
+    return d[None, :] * (1.0 - 2.0 * par)
+
+
 def levels(seed, k, row_offset, m, stream=0, rows=None, dist=GAUSSIAN):
-    """Theta / scale(k, dist): the integer levels (Gaussian table) or the signs (Rademacher)."""
+    """Theta / scale(k, dist): the integer levels (Gaussian table) or the signs (Rademacher, SRHT)."""
     if dist == RADEMACHER:
         return rademacher_signs(seed, k, row_offset, m, stream, rows)
+    if dist == SRHT:
+        return srht_signs(seed, k, row_offset, m, stream, rows)
     return theta_levels(seed, k, row_offset, m, stream, rows)
 
 
 def scale(k, dist=GAUSSIAN):
     """Theta = scale(k, dist) * levels(...): 1/sqrt(k v) (Gaussian table) or 1/sqrt(k)."""
-    return 1.0 / np.sqrt(float(k)) if dist == RADEMACHER else theta_scale(k)
+    return 1.0 / np.sqrt(float(k)) if dist in (RADEMACHER, SRHT) else theta_scale(k)
 
 
 def dense(seed, k, row_offset, m, stream=0, dist=GAUSSIAN):

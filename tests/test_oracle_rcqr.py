@@ -234,6 +234,27 @@ def test_rademacher_sketch_exact_on_integers_bruteforce():
     assert np.array_equal(P, (1.0 / np.sqrt(k)) * np.array(exact, dtype=np.float64))
 
 
+def test_srht_sketch_exact_on_integers_bruteforce():
+    # the SRHT through the same row-blocked sketch: sqrt(k) P is the integer product S H D X
+    rng = np.random.default_rng(23)
+    m, n, k, seed, off = 301, 3, 20, 98765, 45
+    X = rng.integers(-128, 128, size=(m, n))
+    Sg = theta.srht_signs(seed, k, off, m).astype(np.int64)
+    exact = [[sum(int(Sg[i, r]) * int(X[r, j]) for r in range(m)) for j in range(n)] for i in range(k)]
+    P = rcqr.sketch(X.astype(np.float64), k, seed, row_offset=off, dist=theta.SRHT, row_block=64)
+    assert np.array_equal(P, (1.0 / np.sqrt(k)) * np.array(exact, dtype=np.float64))
+
+
+def test_rcholqr2_with_srht_theta():
+    # an SRHT embedding serves Alg. 3 like the Gaussian one (Sec. 2; the paper's figures use it)
+    m, n, k, kappa = 3000, 10, 80, 1e6
+    X, _ = svd_matrix(m, n, kappa, 29)
+    Q, R, _ = rcqr.rcholqr2(X, k, 9, dist=theta.SRHT)
+    _, Rh = linalg.householder_qr(X)
+    assert rcqr.orthogonality(Q) <= 100 * n * U64
+    assert np.max(np.abs(R - Rh) / np.abs(Rh).max(axis=0)[None, :]) <= 10 * n * U64 * kappa
+
+
 def test_rcholqr2_with_rademacher_theta():
     # a Rademacher embedding serves Alg. 3 like the Gaussian one: R equals Householder R of X
     m, n, k, kappa = 3000, 10, 80, 1e6

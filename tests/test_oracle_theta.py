@@ -129,3 +129,51 @@ def test_rademacher_theta_unit_columns_and_balance():
     s = np.sign(Th)
     assert abs(np.mean(s)) < 0.02                                            # +-1 balanced
     assert abs(np.mean(s[:, :-1] * s[:, 1:])) < 0.02                         # no pairing of neighbours
+
+
+def _scalar_bit(seed, q, row, stream, b):
+    """Bit b (0..127) of the Philox4x32-10 output at counter (q lo, q hi, row, stream)."""
+    from oracle.philox import philox4x32_10
+    w = philox4x32_10(np.uint64(q & 0xFFFFFFFF), np.uint64(q >> 32), np.uint64(row), np.uint64(stream),
+                      seed & 0xFFFFFFFF, seed >> 32)
+    return (int(w[b // 32]) >> (b % 32)) & 1
+
+
+def test_srht_is_random_signs_times_sampled_sylvester_hadamard_rows():
+    # Theta(i, r) sqrt(k) = d_r H(h_i, r): H from scipy's Sylvester construction (independent of
+    # the oracle's popcount), d_r and h_i recomputed entry by entry from scalar Philox calls
+    from scipy.linalg import hadamard
+    from oracle.philox import philox4x32_10
+    seed, k, off, m, stream = 0x0DDC0FFEE1234567, 7, 77, 300, 2
+    S = theta.srht_signs(seed, k, off, m, stream)
+    H = hadamard(1024)                       # rows off .. off+m-1 < 1024: only h mod 1024 matters
+    for i in range(k):
+        w = philox4x32_10(np.uint64(i), np.uint64(0), np.uint64(0xFFFFFFFE), np.uint64(stream),
+                          seed & 0xFFFFFFFF, seed >> 32)
+        h = int(w[0]) | (int(w[1]) << 32)
+        for r in range(off, off + m, 7):
+            d = 1 - 2 * _scalar_bit(seed, r // 128, 0xFFFFFFFF, stream, r % 128)
+            assert S[i, r - off] == d * H[h % 1024, r]
+    assert np.array_equal(theta.srht_signs(seed, k, off, m, stream, rows=[5, 0]), S[[5, 0]])
+    assert np.array_equal(theta.srht_signs(seed, k, off + 10, 20, stream), S[:, 10:30])
+
+
+def test_srht_rows_are_exactly_orthogonal_over_aligned_blocks():
+    # Over the 2^p aligned rows r = q 2^p + j of X the signs cancel in Theta Theta^T and the
+    # Hadamard rows are orthogonal: k (Theta Theta^T)(i, j) = 0 unless h_i = h_j (mod 2^p), and
+    # then +-2^p with the sign (-1)^popcount((h_i XOR h_j) AND q 2^p) -- exactly
+    seed, k, p, q = 4242, 40, 9, 3
+    L = theta.levels(seed, k, q * 2 ** p, 2 ** p, dist=theta.SRHT)      # sqrt(k) Theta: +-1
+    h = [int(v) for v in theta.srht_rows(seed, k)]
+    G = L @ L.T
+    for a in range(k):
+        for b in range(k):
+            same = (h[a] - h[b]) % 2 ** p == 0
+            sign = -1.0 if bin((h[a] ^ h[b]) & (q * 2 ** p)).count("1") % 2 else 1.0
+            assert G[a, b] == (sign * 2 ** p if same else 0.0)
+    assert np.sum(G != 0) > k                                         # some rows do coincide mod 2^p
+    # unit columns exactly; E[Theta^T Theta] = I (off-diagonal ~ 1/sqrt(k) for many rows)
+    Th = theta.dense(seed, 4096, 5, 48, dist=theta.SRHT)
+    C = Th.T @ Th
+    assert np.allclose(np.diag(C), 1.0, rtol=0, atol=1e-15)
+    assert np.max(np.abs(C - np.eye(48))) < 6.0 / math.sqrt(4096)
