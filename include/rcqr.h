@@ -76,8 +76,15 @@ typedef enum { RCQR_F64 = 0, RCQR_F32 = 1, RCQR_BF16 = 2 } rcqr_prec;
  * (1 - 2 b) / sqrt(k) with b = bit (r mod 128) of Philox4x32-10(counter =
  * (floor(r/128) mod 2^32, floor(r/128) div 2^32, i, stream), key = (seed mod 2^32,
  * seed div 2^32)), bit b of the 128-bit output being bit (b mod 32) of word
- * floor(b/32): one Philox bit per entry. */
-typedef enum { RCQR_THETA_GAUSSIAN = 0, RCQR_THETA_RADEMACHER = 1 } rcqr_theta;
+ * floor(b/32): one Philox bit per entry.  RCQR_THETA_SRHT: the subsampled randomized
+ * Hadamard transform sqrt(1/k) S H D of Sec. 2, X padded with zero rows to 2^64 rows:
+ * entry (i, r) = (1 - 2 s_r) (-1)^popcount(h_i AND r) / sqrt(k), where s_r is the
+ * Rademacher bit above taken at the row index i = 2^32 - 1 (the random signs D, the same
+ * for every row of Theta) and h_i = w0 + 2^32 w1, (w0, w1) the first two words of
+ * Philox4x32-10(counter = (i, 0, 2^32 - 2, stream), same key): uniform sampling S of the
+ * rows of the Sylvester-Hadamard matrix H, with replacement.  It is applied as the dense
+ * +-1 product, exactly like the Rademacher one. */
+typedef enum { RCQR_THETA_GAUSSIAN = 0, RCQR_THETA_RADEMACHER = 1, RCQR_THETA_SRHT = 2 } rcqr_theta;
 
 /* Diagnostics: the bound of every device-side wait in the tensor-core
  * sketch's pipeline, in rounds of one mbarrier poll and a sleep of at most

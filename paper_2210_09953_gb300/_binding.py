@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "librcqr.so")
 
 F64, F32, BF16 = 0, 1, 2
 DIRECT, DIRECT2, RR, RR2, SRR, SRR2 = 0, 1, 2, 3, 4, 5
-THETA_GAUSSIAN, THETA_RADEMACHER = 0, 1
+THETA_GAUSSIAN, THETA_RADEMACHER, THETA_SRHT = 0, 1, 2
 STATUS_NAMES = {0: "RCQR_OK", -1: "RCQR_EINVAL", -2: "RCQR_ENOTSPD", -3: "RCQR_ERANK0",
                 -4: "RCQR_ECUDA", -5: "RCQR_ETIMEOUT", -6: "RCQR_EWORKSPACE", -7: "RCQR_EUNSUPPORTED"}
 

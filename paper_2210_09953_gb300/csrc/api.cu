@@ -42,7 +42,9 @@ namespace {
 
 bool valid_prec(int prec) { return prec == RCQR_F64 || prec == RCQR_F32 || prec == RCQR_BF16; }
 
-bool valid_theta(int theta) { return theta == RCQR_THETA_GAUSSIAN || theta == RCQR_THETA_RADEMACHER; }
+bool valid_theta(int theta) {
+  return theta == RCQR_THETA_GAUSSIAN || theta == RCQR_THETA_RADEMACHER || theta == RCQR_THETA_SRHT;
+}
 
 bool valid_sizes(int64_t m, int64_t n, int64_t k) {
   return m >= 1 && n >= 1 && n <= 256 && k >= n && k <= 2048 && (k % 8) == 0;

@@ -352,31 +352,51 @@ struct ThetaCalls {
   }
 };
 
-// The Rademacher Theta tile of one stage: thread tt (< KCH * 128) owns Theta row
-// il = tt % 128 of chunk c = tt / 128 (row i = (kgi KCH + c) 128 + il).  Its 32 entries of
-// the stage at global X rows r0 .. r0+31 are bits (r0 mod 128) .. +31 of the Philox call at
-// counter (r0 / 128, i): one call per four stages, kept in registers; bit 0 -> +1, 1 -> -1.
+// The Rademacher or SRHT Theta tile of one stage: thread tt (< KCH * 128) owns Theta row
+// il = tt % 128 of chunk c = tt / 128 (row i = (kgi KCH + c) 128 + il).  Rademacher: its 32
+// entries of the stage at global X rows r0 .. r0+31 are bits (r0 mod 128) .. +31 of the
+// Philox call at counter (r0 / 128, i): one call per four stages, kept in registers.
+// SRHT (Sec. 2, sqrt(1/k) S H D): the same bits of the call at counter (r0 / 128, 2^32 - 1)
+// are the signs d_r, shared by every row, and entry (i, r) flips them by the parity of
+// h_i AND r, h_i = the sampled Hadamard row (words 0, 1 of the call at counter
+// (i, 0, 2^32 - 2)).  With r = r0 + j (r0 a multiple of 32, j < 32) that parity is
+// parity(h_i AND r0) XOR parity(h_i AND j): one popcount per stage and a 32-bit mask of the
+// second term computed once.  Bit 0 -> +1, 1 -> -1.
 template <int KCH>
 struct RadCalls {
   uint32_t row;     // Theta row i (>= k: a zero row)
   uint32_t off;     // byte offset of the row's first 16 bytes in the tile
   uint4 w;
+  bool srht;
+  uint64_t h;       // SRHT: the sampled Hadamard row
+  uint32_t pmask;   // SRHT: bit j = parity(h AND j), j < 32
 
-  __device__ __forceinline__ void init(int tt, int kgi) {
+  __device__ __forceinline__ void init(int tt, int kgi, const TcArgs &a) {
     const int c = tt >> 7, il = tt & 127;
     row = (uint32_t)((kgi * KCH + c) * 128 + il);
     off = (uint32_t)(c * (128 * kBK * 2) + (il >> 3) * (kBK * 16) + (il & 7) * 16);
     w = make_uint4(0u, 0u, 0u, 0u);
+    srht = a.dist == RCQR_THETA_SRHT;
+    h = 0;
+    pmask = 0;
+    if (srht) {
+      const uint4 hw = philox4x32_10_keys(make_uint4(row, 0u, 0xFFFFFFFEu, a.stream_id), a.rk);
+      h = (uint64_t)hw.x | ((uint64_t)hw.y << 32);
+      for (uint32_t j = 0; j < 32; ++j) pmask |= (uint32_t)(__popc((uint32_t)h & j) & 1) << j;
+    }
   }
 
   __device__ __forceinline__ void tile(unsigned char *sA, int64_t r0, const TcArgs &a) {
     const int sub = (int)((r0 >> 5) & 3);          // the call's 32-bit word for these 32 rows
     if (sub == 0) {                                // stages start on 128-row boundaries at sub 0
       const uint64_t q = (uint64_t)(r0 >> 7);
-      w = row < (uint32_t)a.k ? philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), row, a.stream_id), a.rk)
-                              : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t ctr = srht ? 0xFFFFFFFFu : row;
+      w = (srht || row < (uint32_t)a.k)
+              ? philox4x32_10_keys(make_uint4((uint32_t)q, (uint32_t)(q >> 32), ctr, a.stream_id), a.rk)
+              : make_uint4(0u, 0u, 0u, 0u);
     }
-    const uint32_t word = sub == 0 ? w.x : (sub == 1 ? w.y : (sub == 2 ? w.z : w.w));
+    uint32_t word = sub == 0 ? w.x : (sub == 1 ? w.y : (sub == 2 ? w.z : w.w));
+    if (srht) word ^= pmask ^ ((__popcll(h & (uint64_t)r0) & 1) ? 0xFFFFFFFFu : 0u);
     const bool live = row < (uint32_t)a.k;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
@@ -647,8 +667,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) sketch_tc_kernel(TcArgs a) {
     const uint32_t *tabp = table + lane;
     ThetaCalls<KCH, NTW> calls;
     RadCalls<KCH> rad;
-    const bool rademacher = a.dist == RCQR_THETA_RADEMACHER;
-    if (rademacher) rad.init(tid, kgi);
+    const bool rademacher = a.dist != RCQR_THETA_GAUSSIAN;   // one bit per entry: Rademacher or SRHT
+    if (rademacher) rad.init(tid, kgi, a);
     else calls.init(tid, kgi);
     // ring slot, its phase parity, block and stage within the block, first X row of
     // the stage: all advanced incrementally (blocks are contiguous, so the row is
@@ -1011,7 +1031,7 @@ cudaError_t launch_sketch_tc(const void *X, int64_t m, int64_t n, int64_t ldx, i
     default: e = launch_tc_prec<RCQR_BF16>(a, p, grid, st);
   }
   if (e != cudaSuccess) return e;
-  const double c = dist == RCQR_THETA_RADEMACHER ? 1.0 / std::sqrt((double)k) : theta_scale(k);
+  const double c = dist != RCQR_THETA_GAUSSIAN ? 1.0 / std::sqrt((double)k) : theta_scale(k);
   sketch_tc_reduce_kernel<<<(unsigned)((k * n * 32 + 255) / 256), 256, 0, st>>>(partial, p.groups, (int)k, (int)n,
                                                                           c, P, ldp);
   return cudaGetLastError();

@@ -90,6 +90,12 @@ def test_invalid_arguments_return_einval_without_device(rc):
     assert L.rcqr_trsm(fake, 100, 300, 100, 0, fake, 300, None, None, fake, 100, None, 0, None) == -1
     assert L.rcqr_gram(fake, 100, 4, 50, 0, None, fake, 4, ws, 1 << 30, None) == -1
     assert L.rcqr_chol_update(None, 4, 4, None, fake, 4, fake, 4, None, None) == -1
+    # Theta distributions: Gaussian, Rademacher and SRHT (0, 1, 2) pass the argument check and
+    # fail on the workspace size instead; anything else is EINVAL
+    for theta in (0, 1, 2):
+        assert L.rcqr_sketch_theta(fake, 100, 4, 100, 0, 16, 1, theta, 0, fake, 16, None, ws, 16, None) == -6
+    for theta in (-1, 3):
+        assert L.rcqr_sketch_theta(fake, 100, 4, 100, 0, 16, 1, theta, 0, fake, 16, None, ws, 1 << 30, None) == -1
 
 
 def test_reduced_workspace_counts_the_extractor(rc):
