@@ -215,6 +215,16 @@ def measure_variants(rc, inputs, timed, dev, X32, ws32, Q32):
     Gr = Qr.double().t() @ Qr.double()
     out["rcholqr2_mixed_4Mx64_rademacher"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms),
                                               "orth_QtQ_minus_I": spectral_dev(Gr), "status": int(st_r[0])}
+    # the SRHT (random signs, sampled Hadamard rows), applied as the same +-1 product
+    ms = timed(lambda: rc.rcqr_sketch(X32, K, SEED_THETA, P=P, workspace=ws32, theta=rc.THETA_SRHT), 5, 2)
+    out["sketch_srht_4Mx64"] = {"ms": round(ms, 4), "GB/s": gbs(m * N * 4, ms)}
+    ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32,
+                                      theta=rc.THETA_SRHT), 5, 2)
+    Qr, Rr, _, _, st_r = rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.DIRECT2, Q=Q32, workspace=ws32,
+                                        theta=rc.THETA_SRHT)
+    Gr = Qr.double().t() @ Qr.double()
+    out["rcholqr2_mixed_4Mx64_srht"] = {"ms": round(ms, 3), "GB/s": gbs(m * N * 4, ms),
+                                        "orth_QtQ_minus_I": spectral_dev(Gr), "status": int(st_r[0])}
     del P, Gr
     ws_rr = torch.empty(rc.rcqr_workspace_size(m, N, K, rc.RR2, rc.F32) + 256, dtype=torch.uint8, device=dev)
     ms = timed(lambda: rc.rcqr_factor(X32, K, SEED_THETA, variant=rc.RR2, tau=1e-5, Q=Q32, workspace=ws_rr), 5, 2)
